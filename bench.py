@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark: two-link staggered quark smearing on 64^3 x 96 (arXiv:2301.05518).
+
+One step = the whole hot path through the C ABI on device-resident inputs:
+  tls_load_gauge (ingest the FP64 links)  ->  tls_build_twolink (W in FP64,
+  rounded to the storage type)  ->  tls_smear (24 corner-wall sources, N = 80
+  steps of psi <- psi + sigma/(4N) Delta psi on every slice)  ->  tls_free_gauge.
+value = vectors per second over all ranks.  The timed region is bracketed by a
+barrier and torch.cuda.synchronize() and timed with CUDA events; the inputs
+(14.5 GB of links, 14.5 GB of vectors) are larger than L2, so no flush is
+needed.  Each step smears the previous step's output in place (same work).
+
+`e2e` repeats the step with the links and vectors in pinned host memory: the
+host->device and device->host copies happen inside the C-ABI calls.
+
+`--impl reference` times the FP64 CPU oracle instead (host cores, a bounded
+sample of the same workload per step, extrapolated to vectors/s).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--storage f32|f16|bf16]
+       [--kernel auto|mrhs|persistent|single] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "two-link Laplacian GB/s vs HBM peak & vectors/s at 64^3x96; serving p50/p99 ms"
+UNIT = "vectors/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "single", "mrhs", "persistent"])
+    ap.add_argument("--small", action="store_true", help="16^3x8 lattice, for quick checks only")
+    ap.add_argument("--no-extra", action="store_true", help="skip e2e, cpu baseline and side measurements")
+    return ap.parse_args()
+
+
+def dist_setup(backend):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(small):
+    from paper_2301_05518_gb300 import workloads
+    w = dict(workloads.HEADLINE)
+    if small:
+        w.update(dims=(16, 16, 16, 8), name="16^3x8 24 corner-wall sources N=80 (quick check)")
+    return w
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (clocks and throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def make_inputs(w, device):
+    import torch
+    from paper_2301_05518_gb300 import synth
+    dims = w["dims"]
+    U = synth.gauge_near_unit(dims, w["eps"], w["gauge_seed"], nd=4, device=device)
+    vecs = synth.corner_wall_sources(dims, t=0, dtype=torch.complex64, device=device)
+    return U, vecs
+
+
+def cpu_sample(w, U_host_slices, nsl, n_steps):
+    """Time the FP64 oracle on nsl slices x 1 vector; returns (seconds, threads)."""
+    import numpy as np
+    import oracle
+    from paper_2301_05518_gb300 import synth
+    dims = (w["dims"][0], w["dims"][1], w["dims"][2], nsl)
+    src = synth.corner_wall_sources(dims, t=0).numpy()[0:1]
+    t0 = time.perf_counter()
+    W = oracle.twolink(U_host_slices)
+    oracle.smear(W, src, n_steps, w["sigma"] * n_steps / w["N"])
+    dt = time.perf_counter() - t0
+    return dt, oracle.threads()
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle on the host cores, a bounded sample per step."""
+    ws, rank, local = dist_setup("gloo")
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2301_05518_gb300 import synth
+    w = workload(args.small)
+    oracle.build()
+    Lx, Ly, Lz, Lt = w["dims"]
+    nsl = 4
+    U = synth.gauge_near_unit((Lx, Ly, Lz, nsl), w["eps"], w["gauge_seed"], nd=4).numpy()
+    n_steps = w["N"]
+    times = []
+    threads = 1
+    for k in range(args.warmup + args.steps):
+        dt, threads = cpu_sample(w, U, nsl, n_steps)
+        if k >= args.warmup:
+            times.append(dt)
+    per = statistics.mean(times)
+    # one sample = 1 vector on nsl of Lt slices with all N steps
+    vec_per_s = (nsl / Lt) / per
+    sample = "1 of %d vectors on %d of %d slices, all %d steps, FP64 (twolink + smear)" % (
+        w["nvec"], nsl, Lt, n_steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": vec_per_s, "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "lattice": list(w["dims"]), "nvec": w["nvec"], "N": w["N"],
+                   "sigma": w["sigma"]},
+        "cpu_baseline": {"value": vec_per_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": vec_per_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def our_arm(args):
+    import torch
+    ws, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    from paper_2301_05518_gb300 import tls
+    T = tls
+    w = workload(args.small)
+    dims = w["dims"]
+    Lx, Ly, Lz, Lt = dims
+    V = Lx * Ly * Lz * Lt
+    storage = {"f32": T.TLS_F32, "f16": T.TLS_F16, "bf16": T.TLS_BF16}[args.storage]
+    wprec = T.TLS_F32
+    kernel = {"auto": T.TLS_KERNEL_AUTO, "single": T.TLS_KERNEL_SINGLE, "mrhs": T.TLS_KERNEL_MRHS,
+              "persistent": T.TLS_KERNEL_PERSISTENT}[args.kernel]
+    N, sigma, nvec = w["N"], w["sigma"], w["nvec"]
+    hbm_peak, peak_kind = load_peaks()
+
+    U, vecs = make_inputs(w, "cuda")
+    torch.cuda.synchronize()
+    ctx = tls.Context(local)
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream()
+
+    launches_per_step = [0]
+    prof_last = {}
+
+    def step(Uin, x):
+        gid = ctx.load_gauge(Uin, 4, dims, stream=stream)
+        ctx.build_twolink(gid, wprec, T.TLS_R18, keep_U=0, stream=stream)
+        pb = ctx.get_profile()
+        ctx.smear(gid, x, T.TLS_F32, nvec, N, sigma, timeslice=T.TLS_ALL_T, storage=storage,
+                  kernel=kernel, stream=stream)
+        p = ctx.get_profile()
+        ctx.free_gauge(gid)
+        launches_per_step[0] = 1 + pb["launches"] + p["launches"]
+        prof_last.update(p)
+        prof_last["ms_build"] = pb["ms_build"]
+        return p
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step(U, vecs)
+    iter_ms = []
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        p = step(U, vecs)
+        iter_ms.append(p["ms_iter"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    t_local = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    ms_per_step = ms_max / args.steps
+    value = ws * nvec * args.steps / (ms_max / 1e3)
+
+    # dominant kernel: the smearing iterations (per-launch average over the timed steps)
+    iter_launches = prof_last["iter_launches"]
+    mean_iter_ms = statistics.mean(iter_ms)
+    per_launch_ms = mean_iter_ms / max(1, iter_launches)
+    per_launch_bytes = prof_last["iter_bytes"] / max(1, iter_launches)
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+    kern_name = {1: "single", 2: "mrhs", 3: "persistent"}.get(prof_last["kernel"], "?")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": None,
+            "kernel": "k_%s" % ("persist" if kern_name == "persistent" else "step"),
+            "peak_source": peak_kind,
+            "note": ("algorithmic bytes = W once + psi read once + psi written once per site and "
+                     "step; persistent launches count all N steps (effective GB/s)")}
+
+    extra = {"breakdown_ms": {k: prof_last[k] for k in ("ms_pack", "ms_iter", "ms_unpack")},
+             "build_ms": prof_last["ms_build"], "kernel": kern_name,
+             "vecs_per_thread": prof_last["vecs_per_thread"]}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": w["name"], "lattice": list(dims), "nvec": nvec, "N": N, "sigma": sigma,
+                   "links": "near-unit exp(i 0.2 H), seed %d" % w["gauge_seed"],
+                   "storage": args.storage, "w_format": "f32-18 (built in f64)", "kernel": kern_name,
+                   "l2": "inputs larger than L2 (no flush)",
+                   "step": "load_gauge + build_twolink + smear(24 vecs, N=80, all slices) + free_gauge",
+                   "parallelism": "replicas x%d" % ws},
+        "roofline": roof,
+        "gpu_launches": launches_per_step[0] * args.steps,
+        "clocks": clk,
+    }
+
+    if not args.no_extra:
+        # end to end through the C ABI with host buffers (pinned)
+        Uh = U.cpu().pin_memory()
+        xh = vecs.cpu().pin_memory()
+        ctx_e2e = ctx
+        t_e2e = []
+        for k in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gid = ctx_e2e.load_gauge(Uh, 4, dims)
+            ctx_e2e.build_twolink(gid, wprec, T.TLS_R18, keep_U=0)
+            n2 = ctx_e2e.smear(gid, xh, T.TLS_F32, nvec, N, sigma, storage=storage, kernel=kernel, norms=True)
+            ctx_e2e.free_gauge(gid)
+            t_e2e.append(time.perf_counter() - t0)
+        e2e_s = statistics.mean(t_e2e[1:])
+        result["e2e"] = {"value": nvec * ws / e2e_s, "unit": UNIT,
+                         "h2d_bytes_per_step": int(Uh.numel() * 16 + xh.numel() * 8),
+                         "d2h_bytes_per_step": int(xh.numel() * 8 + nvec * 8),
+                         "ms_per_step": e2e_s * 1e3}
+        del Uh, xh
+        # single-vector FP32 stencil GB/s (the 70% gate) on the same lattice
+        gid = ctx.load_gauge(U, 4, dims, stream=stream)
+        ctx.build_twolink(gid, T.TLS_F32, T.TLS_R18, keep_U=0, stream=stream)
+        x1 = vecs[:1].clone()
+        single = {}
+        for kname, kk in (("mrhs", T.TLS_KERNEL_MRHS), ("persistent", T.TLS_KERNEL_PERSISTENT)):
+            ctx.smear(gid, x1, T.TLS_F32, 1, 20, 4.0, storage=T.TLS_F32, kernel=kk, stream=stream)
+            p = ctx.get_profile()
+            gbs = p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9
+            single[kname] = {"gbs": gbs, "frac": gbs / hbm_peak, "ms_per_step": p["ms_iter"] / 20}
+        extra["single_rhs_f32_N20"] = single
+        ctx.free_gauge(gid)
+        if rank == 0 and ws >= 1:
+            # CPU baseline: the oracle on a bounded sample, on this machine's host cores
+            Lx, Ly, Lz, Lt = dims
+            nsl = 8
+            Uh1 = U[:nsl].cpu().numpy()
+            dt, threads = cpu_sample(w, Uh1, nsl, N)
+            vps = (nsl / Lt) / dt
+            result["cpu_baseline"] = {"value": vps, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                      "sample": "1 of %d vectors on %d of %d slices, all %d steps, FP64 "
+                                                "(twolink + smear), %.1f s" % (nvec, nsl, Lt, N, dt)}
+    result["extra"] = extra
+    if rank == 0:
+        print(json.dumps(result))
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

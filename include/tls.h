@@ -1,0 +1,245 @@
+/*
+ * tls.h -- C ABI of the GB300 two-link staggered quark smearing library.
+ *
+ * The method (Gottlieb, Jeong, Strelchenko, arXiv:2301.05518, Sec. 2-3):
+ *
+ *   two-link product    W_i(x) = U_i(x) U_i(x + i),  i = x, y, z
+ *                       (Sec. 2, the definition before Eq. tlLapl1)
+ *   two-link Laplacian  Delta psi(x) = 4 Lap_two psi(x)
+ *                         = sum_i [ W_i(x) psi(x + 2i) + W_i^dag(x - 2i) psi(x - 2i) ]
+ *                           - 6 psi(x)                     (Sec. 2, Eq. tlLapl1)
+ *   smearing            psi <- (1 + (sigma/N) Lap_two)^N psi   (Sec. 2, Eq. tlSmear)
+ *                       = N steps of psi <- psi + (sigma / (4N)) Delta psi
+ *   reuse               W is computed once per gauge field and reused for
+ *                       every iteration, source and sink     (Sec. 3)
+ *
+ * Every entry point returns a tls_status: TLS_OK (0) or a negative code.  No
+ * entry point aborts or throws across the ABI.  tls_last_error() gives a
+ * message for the last failing call on the calling thread.
+ *
+ * Layouts seen by the caller (all "canonical", x fastest):
+ *   gauge links U : double [Lt][Lz][Ly][Lx][nd][3][3][2], nd = 3 (mu = x, y, z)
+ *                   or 4 (mu = x, y, z, t; the t links are ignored)
+ *   vectors       : [nvec][Lt][Lz][Ly][Lx][3][2] of double (TLS_F64) or float
+ *                   (TLS_F32); a colour vector of 3 complex numbers per site.
+ * dims[4] = {Lx, Ly, Lz, Lt}.  Every spatial extent must be even (the +-2
+ * hops must keep the 8 spatial-parity sublattices apart, Sec. 2: the operator
+ * preserves taste); Lt >= 1.  Boundaries are periodic in x, y, z; t is never
+ * shifted, every time slice is an independent problem.
+ *
+ * Threads: one tls_ctx may be used from several host threads; calls on one
+ * context are serialised internally.  Streams: a NULL stream means the CUDA
+ * legacy default stream of the context's device.
+ */
+#ifndef TLS_H
+#define TLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tls_ctx tls_ctx;
+typedef int64_t tls_gauge_id;
+typedef int tls_status;
+
+/* ---- status codes ------------------------------------------------------- */
+#define TLS_OK               0
+#define TLS_ERR_ARG         -1  /* invalid argument (odd extent, N < 0, ...)  */
+#define TLS_ERR_NOMEM       -2  /* cudaMalloc failed                          */
+#define TLS_ERR_ADMIT       -3  /* would exceed the context's HBM cap         */
+#define TLS_ERR_CUDA        -4  /* a CUDA runtime call failed                 */
+#define TLS_ERR_TIMEOUT     -5  /* a bounded device wait ran out              */
+#define TLS_ERR_NOT_BUILT   -6  /* smear requested before tls_build_twolink   */
+#define TLS_ERR_DEVICE      -7  /* the device error word was set by a kernel  */
+#define TLS_ERR_STATE       -8  /* call not valid in the current state        */
+#define TLS_ERR_UNSUPPORTED -9  /* precision / recon / kernel combination     */
+#define TLS_ERR_NOT_FOUND  -10  /* unknown gauge id or job id                 */
+
+/* ---- precisions (storage and I/O) ---------------------------------------- */
+#define TLS_F64  0
+#define TLS_F32  1
+#define TLS_F16  2  /* 16-bit storage with one FP32 scale per site and vector */
+#define TLS_BF16 3
+
+/* ---- W compression: reals stored per 3x3 complex matrix ------------------ */
+#define TLS_R18 18  /* all 9 complex entries                                  */
+#define TLS_R12 12  /* rows 1-2; row 3 = conj(row1 x row2) (W is SU(3))       */
+#define TLS_R8   8  /* W01, W02, W10, arg W00, arg W20; needs |W00| < 1       */
+
+/* ---- kernel choice for tls_smear ----------------------------------------- */
+#define TLS_KERNEL_AUTO       0  /* planner / autotune table decides          */
+#define TLS_KERNEL_SINGLE     1  /* one vector per launch, one launch per step */
+#define TLS_KERNEL_MRHS       2  /* all vectors in one launch: W read once     */
+#define TLS_KERNEL_PERSISTENT 3  /* all N steps in one cooperative launch,     */
+                                 /* tiles kept L2-resident between steps       */
+
+#define TLS_ALL_T (-1)           /* timeslice argument: smear every slice      */
+
+/* ---- context -------------------------------------------------------------
+ * tls_create: a context on CUDA device `device`.  hbm_cap_bytes bounds the
+ * device memory the context may hold (gauge fields, two-link fields, vector
+ * workspaces, serving slots); 0 means no cap.  *out is NULL on failure.
+ * tls_destroy frees everything the context owns (stops serving first).   */
+tls_status tls_create(tls_ctx **out, int device, uint64_t hbm_cap_bytes);
+void tls_destroy(tls_ctx *ctx);
+
+/* Message of the last failing tls_* call on this host thread ("" if none).
+ * The pointer stays valid until the next tls_* call on the same thread.   */
+const char *tls_last_error(void);
+
+/* Library version, e.g. 10000 for 1.0.0. */
+int tls_version(void);
+
+/* Device bytes currently held by the context. */
+uint64_t tls_bytes_in_use(const tls_ctx *ctx);
+
+/* ---- gauge field ingest (Sec. 2: U_mu(x)) ----------------------------------
+ * Copies the spatial links of U (layout above, FP64) to the device and
+ * permutes them into the library's sublattice layout (bit-exact).  U is a
+ * device pointer if on_device != 0, else a host pointer; the caller keeps
+ * ownership and may free it when the call returns.  The work is enqueued on
+ * `stream` and finished before return.  Returns the new id in *out.
+ * Errors: TLS_ERR_ARG (nd not 3/4, odd or non-positive extent, more than
+ * 2^31 sites), TLS_ERR_ADMIT, TLS_ERR_NOMEM, TLS_ERR_CUDA.                  */
+tls_status tls_load_gauge(tls_ctx *ctx, const double *U, int nd, const int dims[4],
+                          int on_device, void *stream, tls_gauge_id *out);
+
+/* ---- two-link build (Sec. 2 definition of V_mu; Sec. 3 precompute) ---------
+ * W_i(x) = U_i(x) U_i(x+i) for every site and i = x, y, z, formed in FP64
+ * and rounded to nearest in `wprec` (TLS_F64, TLS_F32, TLS_F16, TLS_BF16),
+ * stored with `recon` reals per matrix (TLS_R18; TLS_R12 or TLS_R8 for FP32;
+ * TLS_R12 for 16-bit).  W stays resident until tls_free_gauge.  keep_U = 0
+ * releases the device copy of U after the build.  Rebuilding replaces W.
+ * Errors: TLS_ERR_NOT_FOUND, TLS_ERR_STATE (U already released),
+ * TLS_ERR_UNSUPPORTED (combination), TLS_ERR_DEVICE (TLS_R8 met a matrix with
+ * |W00| too close to 1 to parameterise), memory errors.                     */
+tls_status tls_build_twolink(tls_ctx *ctx, tls_gauge_id id, int wprec, int recon,
+                             int keep_U, void *stream);
+
+/* Releases U, W and everything cached for gauge `id`. */
+tls_status tls_free_gauge(tls_ctx *ctx, tls_gauge_id id);
+
+/* Copies W back out in FP64, canonical layout [Lt][Lz][Ly][Lx][3][3][3][2]
+ * (i, row, col, re/im), reconstructing compressed forms.  `out` is a host
+ * pointer (on_device = 0) or device pointer (on_device != 0) of V*162
+ * doubles.  For tests of the build.                                        */
+tls_status tls_export_twolink(tls_ctx *ctx, tls_gauge_id id, double *out, int on_device,
+                              void *stream);
+
+/* Copies the device copy of the spatial links back out in canonical layout
+ * [Lt][Lz][Ly][Lx][3][3][3][2] (bit-exact inverse of the ingest).          */
+tls_status tls_export_gauge(tls_ctx *ctx, tls_gauge_id id, double *out, int on_device,
+                            void *stream);
+
+/* ---- smearing (Sec. 2, Eq. tlSmear with Eq. tlLapl1) -------------------------
+ * Applies psi <- (1 + (width/N) Lap_two)^N psi to each of the nvec vectors in
+ * place.  width is the paper's sigma; each step is
+ *     psi'(x) = psi(x) + (width/(4N)) Delta psi(x)   (out of place, Jacobi).
+ * timeslice in [0, Lt) smears that slice only and leaves the other slices of
+ * `vecs` untouched; TLS_ALL_T smears every slice.
+ *   vecs            caller's vectors, layout above, io_prec TLS_F64 or TLS_F32;
+ *                   device pointer if vecs_on_device != 0, else host pointer
+ *                   (then the host<->device copies happen inside the call).
+ *   storage         precision the iterates are stored in between steps:
+ *                   TLS_F64 (needs an FP64 W), TLS_F32 (FP32 W), TLS_F16 or
+ *                   TLS_BF16 (FP32 or 16-bit W; one FP32 scale per site and
+ *                   vector; arithmetic in FP32).
+ *   kernel          TLS_KERNEL_* above.
+ *   norms_out       NULL or a host array of nvec doubles: ||psi_v||^2 of each
+ *                   smeared vector over the smeared slices, summed in FP64 in
+ *                   a fixed order (deterministic).
+ * N = 0 or width = 0 returns the input unchanged in value, up to one rounding
+ * to `storage` when it is narrower than io_prec.  Each vector's result is
+ * bitwise independent of nvec and of the other vectors for a given (kernel,
+ * storage, W format).  The call is synchronous: it returns when the result is
+ * in `vecs`.
+ * Errors: TLS_ERR_ARG, TLS_ERR_NOT_FOUND, TLS_ERR_NOT_BUILT,
+ * TLS_ERR_UNSUPPORTED, TLS_ERR_TIMEOUT (persistent kernel barrier ran out; the
+ * vectors are then unspecified), TLS_ERR_DEVICE, memory and CUDA errors.    */
+tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec,
+                     int vecs_on_device, int nvec, int N, double width, int timeslice,
+                     int storage, int kernel, void *stream, double *norms_out);
+
+/* ---- per-call profile ------------------------------------------------------
+ * With profiling on (tls_set_profiling), each tls_smear / tls_build_twolink
+ * records CUDA events on its stream around its phases.                     */
+typedef struct {
+    double ms_total;        /* whole call on its stream                        */
+    double ms_h2d;          /* host->device copy of the vectors (host input)   */
+    double ms_pack;         /* canonical -> sublattice layout (+ quantise)     */
+    double ms_iter;         /* all smearing steps                              */
+    double ms_unpack;       /* sublattice -> canonical (+ norms)               */
+    double ms_d2h;          /* device->host copy of the vectors (host input)   */
+    double ms_build;        /* tls_build_twolink: the build kernel             */
+    int64_t launches;       /* kernel launches of the call                     */
+    int64_t iter_launches;  /* kernel launches in the iteration phase          */
+    double iter_bytes;      /* algorithmic bytes of the iteration phase:
+                               W once + psi read once + psi written once per
+                               site and step                                   */
+    double iter_flops;      /* algorithmic flops of the iteration phase        */
+    int kernel;             /* TLS_KERNEL_* that actually ran                  */
+    int vecs_per_thread;    /* vectors per thread of the stencil kernel        */
+} tls_profile;
+
+tls_status tls_set_profiling(tls_ctx *ctx, int on);
+tls_status tls_get_profile(tls_ctx *ctx, tls_profile *out);
+
+/* Testing hook for the bounded device waits of the persistent kernel: the
+ * spin budget, in polls, of each inter-block barrier (0 restores the default).
+ * A tiny budget forces the TLS_ERR_TIMEOUT path without hanging the GPU.   */
+tls_status tls_set_barrier_budget(tls_ctx *ctx, int64_t polls);
+
+/* ---- serving: continuous batching of smearing jobs (Sec. 6 pattern) ---------
+ * A scheduler thread keeps each gauge field's W resident, admits jobs while
+ * the context's HBM cap allows, packs the vectors of compatible jobs into the
+ * slots of one multi-right-hand-side batch per (gauge id, storage), and
+ * advances every active slot one step per launch with the slot's own alpha =
+ * width/(4N) and remaining step count.  Jobs arriving while others run join
+ * at the next step boundary; finished slots retire and are unpacked.
+ * A job's result is bitwise the same alone and in any mix.                  */
+typedef struct {
+    int max_slots;          /* vectors per batch (per gauge, storage); <= 256  */
+    int steps_per_launch;   /* steps advanced between admission points (>= 1)  */
+    int use_graphs;         /* capture the per-step launches in CUDA graphs    */
+    int reserved[5];
+} tls_serve_opts;
+
+typedef struct {
+    tls_gauge_id gauge;     /* built gauge field                               */
+    void *vecs;             /* host or device vectors, canonical layout;       */
+                            /* borrowed until tls_serve_wait returns           */
+    int vecs_on_device;
+    int io_prec;            /* TLS_F64 or TLS_F32                              */
+    int nvec;               /* >= 1                                            */
+    int N;                  /* smearing steps, >= 0                            */
+    double width;           /* sigma                                           */
+    int timeslice;          /* slice or TLS_ALL_T                              */
+    int storage;            /* TLS_F32, TLS_F16 or TLS_BF16                    */
+    int reserved[4];
+} tls_job;
+
+typedef struct {
+    tls_status status;      /* TLS_OK or the job's error                       */
+    double submit_ms;       /* host clock, ms since tls_serve_start            */
+    double start_ms;        /* first step on the device (admission)            */
+    double done_ms;         /* result in the caller's buffer                   */
+} tls_job_result;
+
+tls_status tls_serve_start(tls_ctx *ctx, const tls_serve_opts *opts);
+tls_status tls_serve_stop(tls_ctx *ctx);
+/* Non-blocking; copies the descriptor.  TLS_ERR_ADMIT if the job can never
+ * fit under the HBM cap.                                                   */
+tls_status tls_serve_submit(tls_ctx *ctx, const tls_job *job, uint64_t *job_id);
+tls_status tls_serve_poll(tls_ctx *ctx, uint64_t job_id, int *done);
+/* Blocks until the job finishes or timeout_s passes (TLS_ERR_TIMEOUT).     */
+tls_status tls_serve_wait(tls_ctx *ctx, uint64_t job_id, double timeout_s,
+                          tls_job_result *result);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TLS_H */

@@ -1,0 +1,686 @@
+// api.cu -- the C ABI (include/tls.h): context, gauge fields, two-link build, smearing.
+//
+// The hot path of the paper (Sec. 2-3): W_i(x) = U_i(x) U_i(x+i) is built once
+// per gauge field and kept resident; each smearing call applies N steps of
+// psi <- psi + (sigma/(4N)) Delta psi (Eq. tlSmear with Eq. tlLapl1) to a
+// batch of vectors.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "api_internal.h"
+
+namespace tls {
+
+static thread_local std::string g_err;
+
+tls_status fail(tls_status code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+tls_status ok()
+{
+    g_err.clear();
+    return TLS_OK;
+}
+
+tls_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? TLS_ERR_NOMEM : TLS_ERR_CUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+tls_status dev_alloc(tls_ctx *ctx, void **p, size_t bytes, const char *what)
+{
+    *p = nullptr;
+    if (bytes == 0) return TLS_OK;
+    if (ctx->cap && ctx->used.load() + bytes > ctx->cap)
+        return fail(TLS_ERR_ADMIT, "%s: %zu bytes would exceed the HBM cap (%llu in use of %llu)", what, bytes,
+                    (unsigned long long)ctx->used.load(), (unsigned long long)ctx->cap);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(TLS_ERR_NOMEM, "%s: cudaMalloc(%zu) failed: %s", what, bytes, cudaGetErrorString(e));
+    }
+    ctx->used += bytes;
+    return TLS_OK;
+}
+
+void dev_free(tls_ctx *ctx, void *p, size_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    ctx->used -= bytes;
+}
+
+tls_status ensure(tls_ctx *ctx, DevBuf &b, size_t bytes, const char *what)
+{
+    if (b.n >= bytes) return TLS_OK;
+    release(ctx, b);
+    tls_status s = dev_alloc(ctx, &b.p, bytes, what);
+    if (s != TLS_OK) return s;
+    b.n = bytes;
+    cudaError_t e = cudaMemset(b.p, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return TLS_OK;
+}
+
+void release(tls_ctx *ctx, DevBuf &b)
+{
+    dev_free(ctx, b.p, b.n);
+    b.p = nullptr;
+    b.n = 0;
+}
+
+static int wfmt_of(int prec, int recon)
+{
+    if (prec == TLS_F64 && recon == TLS_R18) return W_F64_18;
+    if (prec == TLS_F32) return recon == TLS_R18 ? W_F32_18 : recon == TLS_R12 ? W_F32_12 : recon == TLS_R8 ? W_F32_8 : -1;
+    if (prec == TLS_F16) return recon == TLS_R18 ? W_F16_18 : recon == TLS_R12 ? W_F16_12 : -1;
+    if (prec == TLS_BF16) return recon == TLS_R18 ? W_BF16_18 : recon == TLS_R12 ? W_BF16_12 : -1;
+    return -1;
+}
+
+tls_status check_smear_combo(const Gauge &gg, int storage)
+{
+    const int wf = gg.wfmt;
+    bool okc = false;
+    switch (storage) {
+    case TLS_F64: okc = wf == W_F64_18; break;
+    case TLS_F32: okc = wf == W_F32_18 || wf == W_F32_12 || wf == W_F32_8; break;
+    case TLS_F16: okc = wf == W_F32_18 || wf == W_F32_12 || wf == W_F16_18 || wf == W_F16_12; break;
+    case TLS_BF16: okc = wf == W_F32_18 || wf == W_F32_12 || wf == W_BF16_18 || wf == W_BF16_12; break;
+    default: return fail(TLS_ERR_ARG, "storage precision %d is not a TLS_F* value", storage);
+    }
+    if (!okc)
+        return fail(TLS_ERR_UNSUPPORTED, "vector storage %d cannot run with the W format of this gauge (format %d)",
+                    storage, wf);
+    return TLS_OK;
+}
+
+int default_vb(int storage, int nvec)
+{
+    const int cap = storage == TLS_F64 ? 4 : 8;
+    int vb = 1;
+    while (vb < cap && vb < nvec) vb *= 2;
+    return vb;
+}
+
+cudaError_t launch_step(const StepArgs &a)
+{
+    switch (a.prec_in) {
+    case P_F64: return launch_step_f64(a);
+    case P_F32: return launch_step_f32(a);
+    case P_F16: return launch_step_f16(a);
+    case P_BF16: return launch_step_bf16(a);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t launch_persistent(const PersistArgs &a)
+{
+    switch (a.prec) {
+    case P_F64: return launch_persistent_f64(a);
+    case P_F32: return launch_persistent_f32(a);
+    case P_F16: return launch_persistent_f16(a);
+    case P_BF16: return launch_persistent_bf16(a);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+int persistent_occupancy(int wfmt, int prec, int, int vb, int threads)
+{
+    switch (prec) {
+    case P_F64: return persistent_occupancy_f64(wfmt, vb, threads);
+    case P_F32: return persistent_occupancy_f32(wfmt, vb, threads);
+    case P_F16: return persistent_occupancy_f16(wfmt, vb, threads);
+    case P_BF16: return persistent_occupancy_bf16(wfmt, vb, threads);
+    default: return 0;
+    }
+}
+
+static void free_gauge(tls_ctx *ctx, Gauge &gg)
+{
+    dev_free(ctx, gg.Up, gg.Up_bytes);
+    dev_free(ctx, gg.W, gg.W_bytes);
+    gg.Up = nullptr;
+    gg.W = nullptr;
+    gg.Up_bytes = gg.W_bytes = 0;
+    gg.built = false;
+}
+
+static Gauge *find_gauge(tls_ctx *ctx, tls_gauge_id id)
+{
+    auto it = ctx->gauges.find(id);
+    return it == ctx->gauges.end() ? nullptr : &it->second;
+}
+
+static const long long kDefaultBudget = 20000000LL;  // polls of ~64 ns: about a second or more
+
+}  // namespace tls
+
+using namespace tls;
+
+extern "C" {
+
+int tls_version(void) { return 10000; }
+
+const char *tls_last_error(void) { return g_err.c_str(); }
+
+uint64_t tls_bytes_in_use(const tls_ctx *ctx) { return ctx ? ctx->used.load() : 0; }
+
+tls_status tls_create(tls_ctx **out, int device, uint64_t hbm_cap_bytes)
+{
+    if (!out) return fail(TLS_ERR_ARG, "tls_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "tls_create: cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(TLS_ERR_ARG, "tls_create: device %d of %d", device, ndev);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "tls_create: cudaSetDevice");
+    std::unique_ptr<tls_ctx> ctx(new tls_ctx());
+    ctx->device = device;
+    ctx->cap = hbm_cap_bytes;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    tls_status s = dev_alloc(ctx.get(), (void **)&ctx->d_err, 256, "tls_create: error word");
+    if (s != TLS_OK) return s;
+    s = dev_alloc(ctx.get(), (void **)&ctx->d_bar, 256, "tls_create: barrier words");
+    if (s != TLS_OK) {
+        dev_free(ctx.get(), ctx->d_err, 256);
+        return s;
+    }
+    cudaMemset(ctx->d_err, 0, 256);
+    cudaMemset(ctx->d_bar, 0, 256);
+    e = cudaMallocHost(&ctx->h_err, 256);
+    if (e != cudaSuccess) return cuda_fail(e, "tls_create: pinned error word");
+    for (auto &ev : ctx->ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_fail(e, "tls_create: cudaEventCreate");
+    }
+    *out = ctx.release();
+    return ok();
+}
+
+void tls_destroy(tls_ctx *ctx)
+{
+    if (!ctx) return;
+    serve_shutdown(ctx);
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        cudaSetDevice(ctx->device);
+        cudaDeviceSynchronize();
+        for (auto &kv : ctx->gauges) free_gauge(ctx, kv.second);
+        ctx->gauges.clear();
+        for (DevBuf *b : {&ctx->A, &ctx->B, &ctx->S0, &ctx->S1, &ctx->staging, &ctx->alpha, &ctx->partials,
+                          &ctx->norms})
+            release(ctx, *b);
+        dev_free(ctx, ctx->d_err, 256);
+        dev_free(ctx, ctx->d_bar, 256);
+        if (ctx->h_alpha) cudaFreeHost(ctx->h_alpha);
+        if (ctx->h_norms) cudaFreeHost(ctx->h_norms);
+        if (ctx->h_err) cudaFreeHost(ctx->h_err);
+        for (auto &ev : ctx->ev)
+            if (ev) cudaEventDestroy(ev);
+    }
+    delete ctx;
+}
+
+tls_status tls_set_profiling(tls_ctx *ctx, int on)
+{
+    if (!ctx) return fail(TLS_ERR_ARG, "tls_set_profiling: ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->profiling = on != 0;
+    return ok();
+}
+
+tls_status tls_get_profile(tls_ctx *ctx, tls_profile *out)
+{
+    if (!ctx || !out) return fail(TLS_ERR_ARG, "tls_get_profile: NULL argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    *out = ctx->prof;
+    return ok();
+}
+
+tls_status tls_set_barrier_budget(tls_ctx *ctx, int64_t polls)
+{
+    if (!ctx || polls < 0) return fail(TLS_ERR_ARG, "tls_set_barrier_budget: bad argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ctx->barrier_budget = polls;
+    return ok();
+}
+
+tls_status tls_load_gauge(tls_ctx *ctx, const double *U, int nd, const int dims[4], int on_device, void *stream,
+                          tls_gauge_id *out)
+{
+    if (!ctx || !U || !dims || !out) return fail(TLS_ERR_ARG, "tls_load_gauge: NULL argument");
+    if (nd != 3 && nd != 4) return fail(TLS_ERR_ARG, "tls_load_gauge: nd = %d, must be 3 or 4", nd);
+    for (int k = 0; k < 4; ++k)
+        if (dims[k] <= 0) return fail(TLS_ERR_ARG, "tls_load_gauge: dims[%d] = %d", k, dims[k]);
+    for (int k = 0; k < 3; ++k)
+        if (dims[k] & 1)
+            return fail(TLS_ERR_ARG,
+                        "tls_load_gauge: spatial extent dims[%d] = %d is odd; the +-2 hops need even extents", k,
+                        dims[k]);
+    const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V >= (1LL << 31)) return fail(TLS_ERR_ARG, "tls_load_gauge: %lld sites exceed 2^31", (long long)V);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Gauge gg;
+    for (int k = 0; k < 4; ++k) gg.L[k] = dims[k];
+    gg.g.hx = dims[0] / 2;
+    gg.g.hy = dims[1] / 2;
+    gg.g.hz = dims[2] / 2;
+    gg.g.Vs = gg.g.hx * gg.g.hy * gg.g.hz;
+    gg.g.Ps = ((int64_t)gg.g.Vs + 31) / 32 * 32;
+    gg.Up_bytes = (size_t)dims[3] * 8 * 3 * 9 * gg.g.Ps * 16;
+    tls_status s = dev_alloc(ctx, (void **)&gg.Up, gg.Up_bytes, "tls_load_gauge: packed links");
+    if (s != TLS_OK) return s;
+    cudaError_t e = cudaMemsetAsync(gg.Up, 0, gg.Up_bytes, st);
+    const int64_t Vslice = (int64_t)dims[0] * dims[1] * dims[2];
+    const size_t slice_bytes = (size_t)Vslice * nd * 144;
+    if (e == cudaSuccess && on_device) {
+        e = launch_ingest_gauge(U, nd, gg.Up, gg.g, gg.L, st);
+    } else if (e == cudaSuccess) {
+        // Host input: stage a few slices at a time.
+        int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(dims[3], (int64_t)(1ULL << 30) / (int64_t)slice_bytes));
+        void *tmp = nullptr;
+        s = dev_alloc(ctx, &tmp, slice_bytes * chunk, "tls_load_gauge: staging");
+        if (s != TLS_OK) {
+            dev_free(ctx, gg.Up, gg.Up_bytes);
+            return s;
+        }
+        for (int t0 = 0; t0 < dims[3] && e == cudaSuccess; t0 += chunk) {
+            const int nsl = std::min(chunk, dims[3] - t0);
+            e = cudaMemcpyAsync(tmp, (const char *)U + (size_t)t0 * slice_bytes, slice_bytes * nsl,
+                                cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) break;
+            int Lc[4] = {dims[0], dims[1], dims[2], nsl};
+            e = launch_ingest_gauge((const double *)tmp, nd, gg.Up + (size_t)t0 * 8 * 3 * 9 * gg.g.Ps * 2, gg.g, Lc,
+                                    st);
+        }
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = e2;
+        dev_free(ctx, tmp, slice_bytes * chunk);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dev_free(ctx, gg.Up, gg.Up_bytes);
+        return cuda_fail(e, "tls_load_gauge");
+    }
+    const int64_t id = ctx->next_id++;
+    ctx->gauges[id] = gg;
+    *out = id;
+    return ok();
+}
+
+tls_status tls_build_twolink(tls_ctx *ctx, tls_gauge_id id, int wprec, int recon, int keep_U, void *stream)
+{
+    if (!ctx) return fail(TLS_ERR_ARG, "tls_build_twolink: ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    Gauge *gg = find_gauge(ctx, id);
+    if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_build_twolink: unknown gauge id %lld", (long long)id);
+    if (!gg->Up) return fail(TLS_ERR_STATE, "tls_build_twolink: the links of gauge %lld were released", (long long)id);
+    const int wf = wfmt_of(wprec, recon);
+    if (wf < 0) return fail(TLS_ERR_UNSUPPORTED, "tls_build_twolink: precision %d with %d reals", wprec, recon);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nblk = gg->L[3] * 8;
+    const size_t wbytes = (size_t)nblk * 3 * gg->g.Ps * wfmt_bytes(wf);
+    if (gg->W && gg->W_bytes != wbytes) {
+        dev_free(ctx, gg->W, gg->W_bytes);
+        gg->W = nullptr;
+        gg->W_bytes = 0;
+    }
+    gg->built = false;
+    if (!gg->W) {
+        tls_status s = dev_alloc(ctx, (void **)&gg->W, wbytes, "tls_build_twolink: W");
+        if (s != TLS_OK) return s;
+        gg->W_bytes = wbytes;
+        cudaMemsetAsync(gg->W, 0, wbytes, st);
+    }
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st);
+    if (ctx->profiling) cudaEventRecord(ctx->ev[0], st);
+    cudaError_t e = launch_build_twolink(gg->Up, gg->W, wf, gg->g, nblk, ctx->d_err, st);
+    if (ctx->profiling) cudaEventRecord(ctx->ev[1], st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "tls_build_twolink");
+    if (ctx->profiling) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+        ctx->prof = tls_profile{};
+        ctx->prof.ms_build = ms;
+        ctx->prof.ms_total = ms;
+        ctx->prof.launches = 1;
+    }
+    if (herr & DERR_RECON8)
+        return fail(TLS_ERR_DEVICE, "tls_build_twolink: a two-link matrix has |W00| too close to 1 for the 8-real form");
+    gg->wfmt = wf;
+    gg->built = true;
+    if (!keep_U) {
+        dev_free(ctx, gg->Up, gg->Up_bytes);
+        gg->Up = nullptr;
+        gg->Up_bytes = 0;
+    }
+    return ok();
+}
+
+tls_status tls_free_gauge(tls_ctx *ctx, tls_gauge_id id)
+{
+    if (!ctx) return fail(TLS_ERR_ARG, "tls_free_gauge: ctx is NULL");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    Gauge *gg = find_gauge(ctx, id);
+    if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_free_gauge: unknown gauge id %lld", (long long)id);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    free_gauge(ctx, *gg);
+    ctx->gauges.erase(id);
+    return ok();
+}
+
+static tls_status export_common(tls_ctx *ctx, tls_gauge_id id, double *out, int on_device, void *stream, bool w)
+{
+    if (!ctx || !out) return fail(TLS_ERR_ARG, "tls_export: NULL argument");
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    Gauge *gg = find_gauge(ctx, id);
+    if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_export: unknown gauge id %lld", (long long)id);
+    if (w && !gg->built) return fail(TLS_ERR_NOT_BUILT, "tls_export_twolink: W not built");
+    if (!w && !gg->Up) return fail(TLS_ERR_STATE, "tls_export_gauge: links released");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)gg->L[0] * gg->L[1] * gg->L[2] * gg->L[3] * 3 * 144;
+    double *dst = out;
+    void *tmp = nullptr;
+    if (!on_device) {
+        tls_status s = dev_alloc(ctx, &tmp, bytes, "tls_export: staging");
+        if (s != TLS_OK) return s;
+        dst = (double *)tmp;
+    }
+    cudaError_t e = w ? launch_export_twolink(gg->W, gg->wfmt, dst, gg->g, gg->L, st)
+                      : launch_export_gauge(gg->Up, dst, gg->g, gg->L, st);
+    if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (tmp) dev_free(ctx, tmp, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "tls_export");
+    return ok();
+}
+
+tls_status tls_export_twolink(tls_ctx *ctx, tls_gauge_id id, double *out, int on_device, void *stream)
+{
+    return export_common(ctx, id, out, on_device, stream, true);
+}
+
+tls_status tls_export_gauge(tls_ctx *ctx, tls_gauge_id id, double *out, int on_device, void *stream)
+{
+    return export_common(ctx, id, out, on_device, stream, false);
+}
+
+static float elapsed(cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec, int N,
+                     double width, int timeslice, int storage, int kernel, void *stream, double *norms_out)
+{
+    if (!ctx || !vecs) return fail(TLS_ERR_ARG, "tls_smear: NULL argument");
+    if (io_prec != TLS_F64 && io_prec != TLS_F32)
+        return fail(TLS_ERR_ARG, "tls_smear: io_prec %d must be TLS_F64 or TLS_F32", io_prec);
+    if (nvec < 1 || nvec > 65535) return fail(TLS_ERR_ARG, "tls_smear: nvec = %d", nvec);
+    if (N < 0) return fail(TLS_ERR_ARG, "tls_smear: N = %d < 0", N);
+    if (!std::isfinite(width)) return fail(TLS_ERR_ARG, "tls_smear: width is not finite");
+    if (kernel < TLS_KERNEL_AUTO || kernel > TLS_KERNEL_PERSISTENT)
+        return fail(TLS_ERR_ARG, "tls_smear: kernel %d", kernel);
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    Gauge *gg = find_gauge(ctx, id);
+    if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_smear: unknown gauge id %lld", (long long)id);
+    if (!gg->built) return fail(TLS_ERR_NOT_BUILT, "tls_smear: tls_build_twolink has not run for gauge %lld", (long long)id);
+    if (timeslice < TLS_ALL_T || timeslice >= gg->L[3])
+        return fail(TLS_ERR_ARG, "tls_smear: timeslice %d outside [-1, %d)", timeslice, gg->L[3]);
+    tls_status s = check_smear_combo(*gg, storage);
+    if (s != TLS_OK) return s;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    const SubGeom &g = gg->g;
+    const int nsl = timeslice < 0 ? gg->L[3] : 1;
+    const int t_first = timeslice < 0 ? 0 : timeslice;
+    const int nblk = nsl * 8;
+    const int64_t Vslice = (int64_t)gg->L[0] * gg->L[1] * gg->L[2];
+    const int64_t V = Vslice * gg->L[3];
+    const int VBY = vfmt_bytes(storage);
+    const int64_t vs = (int64_t)nblk * g.Ps * VBY;        // packed bytes per vector
+    const size_t io_elem = io_prec == TLS_F64 ? 8 : 4;
+    const size_t io_slice_bytes = (size_t)Vslice * 6 * io_elem;
+
+    // Kernel choice.
+    int kern = kernel;
+    int vb = default_vb(storage, nvec);
+    int threads = 128;
+    if (kern == TLS_KERNEL_AUTO) {
+        TuneKey key{{gg->L[0], gg->L[1], gg->L[2], gg->L[3]}, nsl, nvec, storage, gg->wfmt};
+        auto it = ctx->tune.find(key);
+        if (it != ctx->tune.end()) {
+            kern = it->second.kernel;
+            vb = it->second.vb;
+            threads = it->second.threads;
+        } else {
+            kern = nvec == 1 ? TLS_KERNEL_PERSISTENT : TLS_KERNEL_MRHS;
+        }
+    }
+    if (kern == TLS_KERNEL_SINGLE) vb = 1;
+    if (kern == TLS_KERNEL_PERSISTENT) {
+        threads = 256;
+        if (vb == 2) vb = 1;
+    }
+
+    // Workspace.
+    size_t a_bytes = (size_t)vs * nvec;
+    s = ensure(ctx, ctx->A, a_bytes, "tls_smear: vector buffer A");
+    if (s == TLS_OK) s = ensure(ctx, ctx->B, a_bytes, "tls_smear: vector buffer B");
+    if (s == TLS_OK) s = ensure(ctx, ctx->alpha, sizeof(double) * nvec, "tls_smear: alpha");
+    const int nparts = unpack_parts(g, nsl);
+    if (s == TLS_OK && norms_out) s = ensure(ctx, ctx->partials, sizeof(double) * nparts * nvec, "tls_smear: partials");
+    if (s == TLS_OK && norms_out) s = ensure(ctx, ctx->norms, sizeof(double) * nvec, "tls_smear: norms");
+    if (s == TLS_OK && !vecs_on_device)
+        s = ensure(ctx, ctx->staging, io_slice_bytes * nsl * nvec, "tls_smear: host staging");
+    if (s != TLS_OK) return s;
+    if (ctx->h_alpha_n < (size_t)nvec) {
+        if (ctx->h_alpha) cudaFreeHost(ctx->h_alpha);
+        ctx->h_alpha = nullptr;
+        cudaError_t e = cudaMallocHost(&ctx->h_alpha, sizeof(double) * nvec);
+        if (e != cudaSuccess) return cuda_fail(e, "tls_smear: pinned alpha");
+        ctx->h_alpha_n = nvec;
+    }
+    if (ctx->h_norms_n < (size_t)nvec) {
+        if (ctx->h_norms) cudaFreeHost(ctx->h_norms);
+        ctx->h_norms = nullptr;
+        cudaError_t e = cudaMallocHost(&ctx->h_norms, sizeof(double) * nvec);
+        if (e != cudaSuccess) return cuda_fail(e, "tls_smear: pinned norms");
+        ctx->h_norms_n = nvec;
+    }
+
+    // Persistent-kernel plan: co-resident grid, L2-sized groups, scratch.
+    PersistArgs pa{};
+    if (kern == TLS_KERNEL_PERSISTENT && N > 0) {
+        const int sprec = storage == TLS_F64 ? P_F64 : P_F32;
+        const int occ = persistent_occupancy(gg->wfmt, storage, sprec, vb, threads);
+        if (occ <= 0) return fail(TLS_ERR_UNSUPPORTED, "tls_smear: persistent kernel cannot be resident");
+        const int SBY = vfmt_bytes(sprec);
+        const double per_blk = (double)g.Ps * (3.0 * wfmt_bytes(gg->wfmt) + 2.0 * nvec * SBY);
+        const double budget = 48.0 * (1 << 20);
+        int gb = (int)std::max(1.0, std::floor(budget / per_blk));
+        const int64_t want_items = (int64_t)occ * ctx->num_sms * threads;
+        const int nchunk = (nvec + vb - 1) / vb;
+        while (gb < nblk && (int64_t)gb * g.Vs * nchunk < want_items) ++gb;
+        gb = std::min(gb, nblk);
+        pa.group_blocks = gb;
+        pa.sstride = (int64_t)gb * g.Ps * SBY;
+        s = ensure(ctx, ctx->S0, (size_t)pa.sstride * nvec, "tls_smear: scratch 0");
+        if (s == TLS_OK) s = ensure(ctx, ctx->S1, (size_t)pa.sstride * nvec, "tls_smear: scratch 1");
+        if (s != TLS_OK) return s;
+        const int64_t items = ((int64_t)gb * g.Vs + 31) / 32 * 32 * nchunk;
+        pa.grid = (int)std::min<int64_t>((int64_t)occ * ctx->num_sms, std::max<int64_t>(1, (items + threads - 1) / threads));
+        pa.sprec = sprec;
+    }
+
+    const double a = N > 0 ? width / (4.0 * N) : 0.0;
+    for (int v = 0; v < nvec; ++v) ctx->h_alpha[v] = a;
+
+    cudaError_t e = cudaSuccess;
+    int64_t launches = 0, iter_launches = 0;
+    const bool prof = ctx->profiling;
+    if (prof) cudaEventRecord(ctx->ev[0], st);
+    e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->alpha.p, ctx->h_alpha, sizeof(double) * nvec, cudaMemcpyHostToDevice, st);
+
+    // Caller buffer (device) or staging copy of the selected slices.
+    const char *src_io = nullptr;
+    char *dst_io = nullptr;
+    int64_t io_vstride_sites = V;  // sites between vectors in the canonical buffer
+    int t_rel = t_first;
+    if (vecs_on_device) {
+        src_io = (const char *)vecs;
+        dst_io = (char *)vecs;
+    } else {
+        const size_t width_b = io_slice_bytes * nsl;
+        const size_t pitch = (size_t)V * 6 * io_elem;
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(ctx->staging.p, width_b, (const char *)vecs + (size_t)t_first * io_slice_bytes, pitch,
+                                  width_b, nvec, cudaMemcpyHostToDevice, st);
+        src_io = (const char *)ctx->staging.p;
+        dst_io = (char *)ctx->staging.p;
+        io_vstride_sites = Vslice * nsl;
+        t_rel = 0;
+    }
+    if (prof) cudaEventRecord(ctx->ev[1], st);
+    if (e == cudaSuccess) {
+        e = launch_pack_vectors(src_io, io_prec, io_vstride_sites, (char *)ctx->A.p, storage, vs, g, gg->L, t_rel,
+                                nsl, nvec, st);
+        ++launches;
+    }
+    if (prof) cudaEventRecord(ctx->ev[2], st);
+
+    const char *W0 = gg->W + (size_t)t_first * 8 * 3 * g.Ps * wfmt_bytes(gg->wfmt);
+    char *result = (char *)ctx->A.p;
+    if (N > 0 && e == cudaSuccess) {
+        if (kern == TLS_KERNEL_PERSISTENT) {
+            pa.W = W0;
+            pa.in = (const char *)ctx->A.p;
+            pa.out = (char *)ctx->B.p;
+            pa.scr[0] = (char *)ctx->S0.p;
+            pa.scr[1] = (char *)ctx->S1.p;
+            pa.alpha = (const double *)ctx->alpha.p;
+            pa.g = g;
+            pa.nblk = nblk;
+            pa.nvec = nvec;
+            pa.N = N;
+            pa.vstride = vs;
+            pa.wfmt = gg->wfmt;
+            pa.prec = storage;
+            pa.vb = vb;
+            pa.threads = threads;
+            pa.bar = ctx->d_bar;
+            pa.err = ctx->d_err;
+            pa.budget = ctx->barrier_budget > 0 ? ctx->barrier_budget : kDefaultBudget;
+            pa.stream = st;
+            e = cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), st);
+            if (e == cudaSuccess) e = launch_persistent(pa);
+            ++launches;
+            ++iter_launches;
+            result = (char *)ctx->B.p;
+        } else {
+            StepArgs sa{};
+            sa.W = W0;
+            sa.g = g;
+            sa.nblk = nblk;
+            sa.wfmt = gg->wfmt;
+            sa.prec_in = sa.prec_out = storage;
+            sa.vb = vb;
+            sa.threads = threads;
+            sa.stream = st;
+            sa.vstride_in = sa.vstride_out = vs;
+            const int groups = kern == TLS_KERNEL_SINGLE ? nvec : 1;
+            sa.nvec = kern == TLS_KERNEL_SINGLE ? 1 : nvec;
+            for (int gi = 0; gi < groups && e == cudaSuccess; ++gi) {
+                char *x = (char *)ctx->A.p + (size_t)gi * vs;
+                char *y = (char *)ctx->B.p + (size_t)gi * vs;
+                for (int it = 0; it < N && e == cudaSuccess; ++it) {
+                    sa.in = (it & 1) ? y : x;
+                    sa.out = (it & 1) ? x : y;
+                    sa.alpha = (const double *)ctx->alpha.p + gi;
+                    e = launch_step(sa);
+                    ++launches;
+                    ++iter_launches;
+                }
+            }
+            result = (N & 1) ? (char *)ctx->B.p : (char *)ctx->A.p;
+        }
+    }
+    if (prof) cudaEventRecord(ctx->ev[3], st);
+    if (e == cudaSuccess) {
+        e = launch_unpack_vectors(result, storage, vs, dst_io, io_prec, io_vstride_sites, g, gg->L, t_rel, nsl, nvec,
+                                  norms_out ? (double *)ctx->partials.p : nullptr, nullptr, st);
+        ++launches;
+    }
+    if (e == cudaSuccess && norms_out) {
+        e = launch_reduce_norms((const double *)ctx->partials.p, nparts, nvec, (double *)ctx->norms.p, st);
+        ++launches;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->h_norms, ctx->norms.p, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st);
+    }
+    if (prof) cudaEventRecord(ctx->ev[4], st);
+    if (e == cudaSuccess && !vecs_on_device) {
+        const size_t width_b = io_slice_bytes * nsl;
+        const size_t pitch = (size_t)V * 6 * io_elem;
+        e = cudaMemcpy2DAsync((char *)vecs + (size_t)t_first * io_slice_bytes, pitch, ctx->staging.p, width_b,
+                              width_b, nvec, cudaMemcpyDeviceToHost, st);
+    }
+    if (prof) cudaEventRecord(ctx->ev[5], st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess) return cuda_fail(e, "tls_smear");
+    herr = *ctx->h_err;
+    if (prof) {
+        tls_profile &p = ctx->prof;
+        p = tls_profile{};
+        p.ms_total = elapsed(ctx->ev[0], ctx->ev[5]);
+        p.ms_h2d = elapsed(ctx->ev[0], ctx->ev[1]);
+        p.ms_pack = elapsed(ctx->ev[1], ctx->ev[2]);
+        p.ms_iter = elapsed(ctx->ev[2], ctx->ev[3]);
+        p.ms_unpack = elapsed(ctx->ev[3], ctx->ev[4]);
+        p.ms_d2h = elapsed(ctx->ev[4], ctx->ev[5]);
+        p.launches = launches;
+        p.iter_launches = iter_launches;
+        const double sites = (double)nblk * g.Vs;
+        const double wb = 3.0 * wfmt_bytes(gg->wfmt), vbb = 2.0 * VBY;
+        p.iter_bytes = kern == TLS_KERNEL_SINGLE ? (double)N * nvec * sites * (wb + vbb)
+                                                 : (double)N * sites * (wb + nvec * vbb);
+        p.iter_flops = 450.0 * N * nvec * sites;
+        p.kernel = kern;
+        p.vecs_per_thread = vb;
+    }
+    if (herr & DERR_TIMEOUT)
+        return fail(TLS_ERR_TIMEOUT, "tls_smear: a bounded inter-block barrier of the persistent kernel ran out");
+    if (herr) return fail(TLS_ERR_DEVICE, "tls_smear: device error word 0x%x", herr);
+    if (norms_out) std::memcpy(norms_out, ctx->h_norms, sizeof(double) * nvec);
+    return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// api_internal.h -- the context object behind the C ABI (shared by api.cu and serve.cpp).
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdarg>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/tls.h"
+#include "tls_internal.h"
+
+namespace tls {
+
+struct Server;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+};
+
+struct Gauge {
+    int L[4] = {0, 0, 0, 0};
+    SubGeom g{};
+    double *Up = nullptr;  // packed spatial links, FP64
+    size_t Up_bytes = 0;
+    char *W = nullptr;     // packed two-link field
+    size_t W_bytes = 0;
+    int wfmt = -1;
+    bool built = false;
+};
+
+// Best kernel per problem shape, filled by tls_autotune-style measurement.
+struct TuneKey {
+    int L[4];
+    int nsl, nvec, storage, wfmt;
+    bool operator<(const TuneKey &o) const
+    {
+        const int a[] = {L[0], L[1], L[2], L[3], nsl, nvec, storage, wfmt};
+        const int b[] = {o.L[0], o.L[1], o.L[2], o.L[3], o.nsl, o.nvec, o.storage, o.wfmt};
+        for (int k = 0; k < 8; ++k)
+            if (a[k] != b[k]) return a[k] < b[k];
+        return false;
+    }
+};
+struct TuneVal {
+    int kernel, vb, threads;
+    double ms;
+};
+
+}  // namespace tls
+
+struct tls_ctx {
+    int device = 0;
+    int num_sms = 0;
+    uint64_t cap = 0;                       // 0 = no cap
+    std::atomic<uint64_t> used{0};
+    std::recursive_mutex mu;                // serialises device work on this context
+    std::map<int64_t, tls::Gauge> gauges;
+    int64_t next_id = 1;
+
+    // smear workspace (grown on demand)
+    tls::DevBuf A, B, S0, S1, staging, alpha, partials, norms;
+    double *h_alpha = nullptr;              // pinned
+    size_t h_alpha_n = 0;
+    double *h_norms = nullptr;              // pinned
+    int *h_err = nullptr;                   // pinned copy of the error word
+    size_t h_norms_n = 0;
+    int *d_err = nullptr;                   // device error word
+    unsigned *d_bar = nullptr;              // barrier words (count, generation)
+    long long barrier_budget = 0;           // 0 = default
+
+    bool profiling = false;
+    tls_profile prof{};
+    cudaEvent_t ev[8] = {};
+
+    std::map<tls::TuneKey, tls::TuneVal> tune;
+
+    tls::Server *server = nullptr;
+};
+
+namespace tls {
+
+// Thread-local error message and status helpers.
+tls_status fail(tls_status code, const char *fmt, ...);
+tls_status ok();
+tls_status cuda_fail(cudaError_t e, const char *what);
+
+// Device memory under the context's cap.
+tls_status dev_alloc(tls_ctx *ctx, void **p, size_t bytes, const char *what);
+void dev_free(tls_ctx *ctx, void *p, size_t bytes);
+tls_status ensure(tls_ctx *ctx, DevBuf &b, size_t bytes, const char *what);
+void release(tls_ctx *ctx, DevBuf &b);
+
+// Shared argument checks for smearing (tls_smear and serving).
+tls_status check_smear_combo(const Gauge &gg, int storage);
+int default_vb(int storage, int nvec);
+
+// The serving subsystem (serve.cpp).
+void serve_shutdown(tls_ctx *ctx);
+
+}  // namespace tls

@@ -1,0 +1,363 @@
+// k_layout.cu -- gauge ingest, two-link build, vector pack/unpack, norms.
+//
+//   ingest      canonical FP64 U[t][z][y][x][mu][3][3] -> sublattice planes
+//               (bit-exact permutation; U_t is never read)
+//   build       W_i(x) = U_i(x) U_i(x+i) in FP64 (Sec. 2), rounded to nearest
+//               into the chosen W storage (Sec. 3: computed once, reused)
+//   pack        caller vectors (FP64/FP32, canonical) -> packed storage
+//   unpack      packed storage -> caller layout, with FP64 |psi|^2 partial sums
+//   norms       fixed-order reduction of the partial sums (deterministic)
+//
+// Packed U layout: block b = t * 8 + sub, direction d, entry k = 0..8:
+//   Up[((b * 3 + d) * 9 + k) * Ps + i]  (double2 = one complex entry)
+#include "tls_dev.cuh"
+#include "tls_internal.h"
+
+namespace tls {
+
+namespace {
+
+struct Coords {
+    int x, y, z;
+};
+
+// Site i of sublattice `sub` -> spatial coordinates.
+__device__ __forceinline__ Coords coords_of(const SubGeom &g, int sub, int i)
+{
+    int xq = i % g.hx;
+    int r = i / g.hx;
+    int yq = r % g.hy;
+    int zq = r / g.hy;
+    Coords c;
+    c.x = 2 * xq + (sub & 1);
+    c.y = 2 * yq + ((sub >> 1) & 1);
+    c.z = 2 * zq + ((sub >> 2) & 1);
+    return c;
+}
+
+__global__ void k_ingest_gauge(const double *__restrict__ U, int nd, double2 *__restrict__ Up, SubGeom g, int Lx,
+                               int Ly, int Lz, int64_t total)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int i = (int)(idx % g.Vs);
+    const int64_t r = idx / g.Vs;
+    const int d = (int)(r % 3);
+    const int b = (int)(r / 3);
+    const int t = b >> 3, sub = b & 7;
+    Coords c = coords_of(g, sub, i);
+    const int64_t site = (((int64_t)t * Lz + c.z) * Ly + c.y) * Lx + c.x;
+    const double2 *src = reinterpret_cast<const double2 *>(U) + (site * nd + d) * 9;
+    double2 *dst = Up + ((int64_t)b * 3 + d) * 9 * g.Ps + i;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dst[k * g.Ps] = src[k];
+}
+
+__global__ void k_export_gauge(const double2 *__restrict__ Up, double *__restrict__ out, SubGeom g, int Lx, int Ly,
+                               int Lz, int64_t total)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int i = (int)(idx % g.Vs);
+    const int64_t r = idx / g.Vs;
+    const int d = (int)(r % 3);
+    const int b = (int)(r / 3);
+    const int t = b >> 3, sub = b & 7;
+    Coords c = coords_of(g, sub, i);
+    const int64_t site = (((int64_t)t * Lz + c.z) * Ly + c.y) * Lx + c.x;
+    double2 *dst = reinterpret_cast<double2 *>(out) + (site * 3 + d) * 9;
+    const double2 *src = Up + ((int64_t)b * 3 + d) * 9 * g.Ps + i;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dst[k] = src[k * g.Ps];
+}
+
+// W_d(x) = U_d(x) U_d(x + d).  In sublattice terms x + d flips bit d of the
+// sublattice index, and the half coordinate advances (with wrap) only when
+// the coordinate was odd.
+template <int WF>
+__global__ void k_build_twolink(const double2 *__restrict__ Up, char *__restrict__ W, SubGeom g, int64_t total,
+                                int *err)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int i = (int)(idx % g.Vs);
+    const int64_t r = idx / g.Vs;
+    const int d = (int)(r % 3);
+    const int b = (int)(r / 3);
+    const int sub = b & 7;
+    int fw[3], bw[3];
+    sub_neighbours(g, i, fw, bw);
+    const int odd = (sub >> d) & 1;
+    const int ip = odd ? fw[d] : i;
+    const int bp = (b & ~7) | (sub ^ (1 << d));
+    const double2 *A = Up + ((int64_t)b * 3 + d) * 9 * g.Ps + i;
+    const double2 *B = Up + ((int64_t)bp * 3 + d) * 9 * g.Ps + ip;
+    double2 a[9], bb[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        a[k] = A[k * g.Ps];
+        bb[k] = B[k * g.Ps];
+    }
+    double w[18];
+#pragma unroll
+    for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            double re = 0.0, im = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double2 x = a[rr * 3 + k], y = bb[k * 3 + cc];
+                re = fma(x.x, y.x, re);
+                re = fma(-x.y, y.y, re);
+                im = fma(x.x, y.y, im);
+                im = fma(x.y, y.x, im);
+            }
+            w[2 * (rr * 3 + cc)] = re;
+            w[2 * (rr * 3 + cc) + 1] = im;
+        }
+    char *blk = W + ((int64_t)b * 3 + d) * g.Ps * wfmt_bytes(WF);
+    if constexpr (WF == W_F32_8) {
+        if (!WFmt<WF>::store(blk, g.Ps, i, w)) atomicOr(err, DERR_RECON8);
+    } else {
+        WFmt<WF>::store(blk, g.Ps, i, w);
+    }
+}
+
+template <int WF>
+__global__ void k_export_twolink(const char *__restrict__ W, double *__restrict__ out, SubGeom g, int Lx, int Ly,
+                                 int Lz, int64_t total)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int i = (int)(idx % g.Vs);
+    const int64_t r = idx / g.Vs;
+    const int d = (int)(r % 3);
+    const int b = (int)(r / 3);
+    const int t = b >> 3, sub = b & 7;
+    Coords c = coords_of(g, sub, i);
+    const int64_t site = (((int64_t)t * Lz + c.z) * Ly + c.y) * Lx + c.x;
+    typedef typename WFmt<WF>::R R;
+    cpx<R> m[9];
+    WFmt<WF>::load(W + ((int64_t)b * 3 + d) * g.Ps * wfmt_bytes(WF), g.Ps, i, m);
+    double *dst = out + ((site * 3 + d) * 9) * 2;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        dst[2 * k] = (double)m[k].re;
+        dst[2 * k + 1] = (double)m[k].im;
+    }
+}
+
+template <typename IO, int VP>
+__global__ void k_pack(const IO *__restrict__ src, int64_t svs, char *__restrict__ dst, int64_t dvs, SubGeom g,
+                       int Lx, int Ly, int Lz, int t_first, int64_t nsite)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsite) return;
+    const int v = blockIdx.y;
+    const int b = (int)(s / g.Vs);
+    const int i = (int)(s - (int64_t)b * g.Vs);
+    const int t = t_first + (b >> 3), sub = b & 7;
+    Coords c = coords_of(g, sub, i);
+    const int64_t site = (((int64_t)t * Lz + c.z) * Ly + c.y) * Lx + c.x;
+    const IO *p = src + ((int64_t)v * svs + site) * 6;
+    typedef typename VFmt<VP>::R R;
+    cpx<R> val[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        val[k].re = (R)p[2 * k];
+        val[k].im = (R)p[2 * k + 1];
+    }
+    VFmt<VP>::template store<false>(dst + (int64_t)v * dvs + (int64_t)b * g.Ps * vfmt_bytes(VP), g.Ps, i, val);
+}
+
+template <typename IO, int VP>
+__global__ void __launch_bounds__(256) k_unpack(const char *__restrict__ src, int64_t svs, IO *__restrict__ dst,
+                                                int64_t dvs, SubGeom g, int Lx, int Ly, int Lz, int t_first,
+                                                int64_t nsite, double *__restrict__ partials)
+{
+    __shared__ double red[256 / 32];
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y;
+    double n2 = 0.0;
+    if (s < nsite) {
+        const int b = (int)(s / g.Vs);
+        const int i = (int)(s - (int64_t)b * g.Vs);
+        const int t = t_first + (b >> 3), sub = b & 7;
+        Coords c = coords_of(g, sub, i);
+        const int64_t site = (((int64_t)t * Lz + c.z) * Ly + c.y) * Lx + c.x;
+        typedef typename VFmt<VP>::R R;
+        cpx<R> val[3];
+        VFmt<VP>::template load<false>(src + (int64_t)v * svs + (int64_t)b * g.Ps * vfmt_bytes(VP), g.Ps, i, val);
+        IO *p = dst + ((int64_t)v * dvs + site) * 6;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const IO re = (IO)val[k].re, im = (IO)val[k].im;
+            p[2 * k] = re;
+            p[2 * k + 1] = im;
+            n2 = fma((double)re, (double)re, n2);
+            n2 = fma((double)im, (double)im, n2);
+        }
+    }
+    if (partials == nullptr) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n2 += __shfl_down_sync(0xffffffffu, n2, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = n2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        partials[(int64_t)v * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+// One CTA per vector sums its partials in a fixed order.
+__global__ void __launch_bounds__(256) k_reduce_norms(const double *__restrict__ partials, int nparts,
+                                                      double *__restrict__ norms)
+{
+    __shared__ double red[256];
+    const int v = blockIdx.x;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) acc += partials[(int64_t)v * nparts + k];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) norms[v] = red[0];
+}
+
+inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename IO>
+cudaError_t pack_io(const IO *src, int64_t svs, char *dst, int prec, int64_t dvs, const SubGeom &g, const int L[4],
+                    int t_first, int64_t nsite, int nvec, cudaStream_t s)
+{
+    dim3 grid(nblocks(nsite, 256), nvec);
+    switch (prec) {
+    case P_F64: k_pack<IO, P_F64><<<grid, 256, 0, s>>>(src, svs, dst, dvs, g, L[0], L[1], L[2], t_first, nsite); break;
+    case P_F32: k_pack<IO, P_F32><<<grid, 256, 0, s>>>(src, svs, dst, dvs, g, L[0], L[1], L[2], t_first, nsite); break;
+    case P_F16: k_pack<IO, P_F16><<<grid, 256, 0, s>>>(src, svs, dst, dvs, g, L[0], L[1], L[2], t_first, nsite); break;
+    case P_BF16: k_pack<IO, P_BF16><<<grid, 256, 0, s>>>(src, svs, dst, dvs, g, L[0], L[1], L[2], t_first, nsite); break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+template <typename IO>
+cudaError_t unpack_io(const char *src, int prec, int64_t svs, IO *dst, int64_t dvs, const SubGeom &g, const int L[4],
+                      int t_first, int64_t nsite, int nvec, double *partials, cudaStream_t s)
+{
+    dim3 grid(nblocks(nsite, 256), nvec);
+    switch (prec) {
+    case P_F64: k_unpack<IO, P_F64><<<grid, 256, 0, s>>>(src, svs, dst, dvs, g, L[0], L[1], L[2], t_first, nsite, partials); break;
+    case P_F32: k_unpack<IO, P_F32><<<grid, 256, 0, s>>>(src, svs, dst, dvs, g, L[0], L[1], L[2], t_first, nsite, partials); break;
+    case P_F16: k_unpack<IO, P_F16><<<grid, 256, 0, s>>>(src, svs, dst, dvs, g, L[0], L[1], L[2], t_first, nsite, partials); break;
+    case P_BF16: k_unpack<IO, P_BF16><<<grid, 256, 0, s>>>(src, svs, dst, dvs, g, L[0], L[1], L[2], t_first, nsite, partials); break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_ingest_gauge(const double *U, int nd, double *Up, const SubGeom &g, const int L[4], cudaStream_t s)
+{
+    const int64_t total = (int64_t)L[3] * 8 * 3 * g.Vs;
+    if (total == 0) return cudaSuccess;
+    k_ingest_gauge<<<nblocks(total, 256), 256, 0, s>>>(U, nd, reinterpret_cast<double2 *>(Up), g, L[0], L[1], L[2],
+                                                       total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_gauge(const double *Up, double *out, const SubGeom &g, const int L[4], cudaStream_t s)
+{
+    const int64_t total = (int64_t)L[3] * 8 * 3 * g.Vs;
+    if (total == 0) return cudaSuccess;
+    k_export_gauge<<<nblocks(total, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(Up), out, g, L[0], L[1],
+                                                       L[2], total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_twolink(const double *Up, char *W, int wfmt, const SubGeom &g, int nblk, int *err,
+                                 cudaStream_t s)
+{
+    const int64_t total = (int64_t)nblk * 3 * g.Vs;
+    if (total == 0) return cudaSuccess;
+    const double2 *u = reinterpret_cast<const double2 *>(Up);
+    const unsigned nb = nblocks(total, 128);
+    switch (wfmt) {
+    case W_F64_18: k_build_twolink<W_F64_18><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
+    case W_F32_18: k_build_twolink<W_F32_18><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
+    case W_F32_12: k_build_twolink<W_F32_12><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
+    case W_F32_8: k_build_twolink<W_F32_8><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
+    case W_F16_18: k_build_twolink<W_F16_18><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
+    case W_F16_12: k_build_twolink<W_F16_12><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
+    case W_BF16_18: k_build_twolink<W_BF16_18><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
+    case W_BF16_12: k_build_twolink<W_BF16_12><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_twolink(const char *W, int wfmt, double *out, const SubGeom &g, const int L[4],
+                                  cudaStream_t s)
+{
+    const int64_t total = (int64_t)L[3] * 8 * 3 * g.Vs;
+    if (total == 0) return cudaSuccess;
+    const unsigned nb = nblocks(total, 128);
+    switch (wfmt) {
+    case W_F64_18: k_export_twolink<W_F64_18><<<nb, 128, 0, s>>>(W, out, g, L[0], L[1], L[2], total); break;
+    case W_F32_18: k_export_twolink<W_F32_18><<<nb, 128, 0, s>>>(W, out, g, L[0], L[1], L[2], total); break;
+    case W_F32_12: k_export_twolink<W_F32_12><<<nb, 128, 0, s>>>(W, out, g, L[0], L[1], L[2], total); break;
+    case W_F32_8: k_export_twolink<W_F32_8><<<nb, 128, 0, s>>>(W, out, g, L[0], L[1], L[2], total); break;
+    case W_F16_18: k_export_twolink<W_F16_18><<<nb, 128, 0, s>>>(W, out, g, L[0], L[1], L[2], total); break;
+    case W_F16_12: k_export_twolink<W_F16_12><<<nb, 128, 0, s>>>(W, out, g, L[0], L[1], L[2], total); break;
+    case W_BF16_18: k_export_twolink<W_BF16_18><<<nb, 128, 0, s>>>(W, out, g, L[0], L[1], L[2], total); break;
+    case W_BF16_12: k_export_twolink<W_BF16_12><<<nb, 128, 0, s>>>(W, out, g, L[0], L[1], L[2], total); break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_vectors(const void *src, int io_prec, int64_t src_vstride_sites, char *dst, int prec,
+                                int64_t dst_vstride, const SubGeom &g, const int L[4], int t_first, int nsl,
+                                int nvec, cudaStream_t s)
+{
+    const int64_t nsite = (int64_t)nsl * 8 * g.Vs;
+    if (nsite == 0 || nvec == 0) return cudaSuccess;
+    if (io_prec == P_F64)
+        return pack_io<double>((const double *)src, src_vstride_sites, dst, prec, dst_vstride, g, L, t_first, nsite,
+                               nvec, s);
+    if (io_prec == P_F32)
+        return pack_io<float>((const float *)src, src_vstride_sites, dst, prec, dst_vstride, g, L, t_first, nsite,
+                              nvec, s);
+    return cudaErrorNotSupported;
+}
+
+int unpack_parts(const SubGeom &g, int nsl) { return (int)nblocks((int64_t)nsl * 8 * g.Vs, 256); }
+
+cudaError_t launch_unpack_vectors(const char *src, int prec, int64_t src_vstride, void *dst, int io_prec,
+                                  int64_t dst_vstride_sites, const SubGeom &g, const int L[4], int t_first,
+                                  int nsl, int nvec, double *partials, int *nparts, cudaStream_t s)
+{
+    const int64_t nsite = (int64_t)nsl * 8 * g.Vs;
+    if (nparts) *nparts = unpack_parts(g, nsl);
+    if (nsite == 0 || nvec == 0) return cudaSuccess;
+    if (io_prec == P_F64)
+        return unpack_io<double>(src, prec, src_vstride, (double *)dst, dst_vstride_sites, g, L, t_first, nsite,
+                                 nvec, partials, s);
+    if (io_prec == P_F32)
+        return unpack_io<float>(src, prec, src_vstride, (float *)dst, dst_vstride_sites, g, L, t_first, nsite, nvec,
+                                partials, s);
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_reduce_norms(const double *partials, int nparts, int nvec, double *norms, cudaStream_t s)
+{
+    if (nvec == 0) return cudaSuccess;
+    k_reduce_norms<<<nvec, 256, 0, s>>>(partials, nparts, norms);
+    return cudaGetLastError();
+}
+
+}  // namespace tls

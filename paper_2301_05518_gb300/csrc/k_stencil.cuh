@@ -1,0 +1,349 @@
+// k_stencil.cuh -- the two-link Laplacian fused with the smearing update.
+//
+// One smearing step (Sec. 2, Eq. tlSmear with Eq. tlLapl1):
+//   psi'(x) = psi(x) + alpha [ sum_i W_i(x) psi(x+2i) + W_i^dag(x-2i) psi(x-2i)
+//                              - 6 psi(x) ],            alpha = sigma / (4N)
+// evaluated out of place.  In the sublattice layout (tls_dev.cuh) the +-2 hops
+// are +-1 steps inside one (slice, sublattice) block, so every operand of a
+// site lives in its own block.
+//
+// Work decomposition: a warp owns 32 consecutive sites of one block and a
+// chunk of VB vectors; the nchunk = ceil(nvec / VB) warps of the same 32 sites
+// are adjacent, so W(x) and W(x-2i) come from DRAM once and are shared through
+// L1/L2 by all vectors (multi-right-hand-side).  VB = 1 with nvec = 1 is the
+// plain single-vector form.
+//
+// This header is included by one translation unit per vector precision
+// (k_step_<prec>.cu) with TLS_VP defined.
+#pragma once
+
+#include "tls_dev.cuh"
+#include "tls_internal.h"
+
+namespace tls {
+
+template <int VP, int WF> __host__ __device__ constexpr bool combo_ok()
+{
+    return VP == P_F64   ? WF == W_F64_18
+         : VP == P_F32   ? (WF == W_F32_18 || WF == W_F32_12 || WF == W_F32_8)
+         : VP == P_F16   ? (WF == W_F32_18 || WF == W_F32_12 || WF == W_F16_18 || WF == W_F16_12)
+         : VP == P_BF16  ? (WF == W_F32_18 || WF == W_F32_12 || WF == W_BF16_18 || WF == W_BF16_12)
+                         : false;
+}
+
+// Scratch precision of the persistent kernel: FP64 stays FP64, everything
+// else keeps FP32 iterates between steps.
+template <int VP> __host__ __device__ constexpr int scratch_prec() { return VP == P_F64 ? P_F64 : P_F32; }
+
+// One site, VB vectors starting at v0.  bin / bout are the byte offsets of the
+// site's block in `in` / `out` (vector 0); wblk is the absolute block for W.
+template <int VPI, int VPO, int WF, int VB, bool CGI, bool CGO>
+__device__ __forceinline__ void site_step(const char *__restrict__ W, const char *__restrict__ in,
+                                          char *__restrict__ out, const double *__restrict__ alpha,
+                                          const SubGeom &g, int wblk, int i, int v0, int nvec, int64_t vs_in,
+                                          int64_t vs_out, int64_t bin, int64_t bout)
+{
+    typedef typename VFmt<VPI>::R R;
+    constexpr int WB = wfmt_bytes(WF);
+    int fw[3], bw[3];
+    sub_neighbours(g, i, fw, bw);
+    const char *wb = W + (int64_t)wblk * 3 * g.Ps * WB;
+    const char *ib = in + bin;
+    cpx<R> acc[VB][3];
+#pragma unroll
+    for (int v = 0; v < VB; ++v)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[v][c].re = acc[v][c].im = R(0);
+
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        cpx<R> m[9];
+        WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, i, m);
+#pragma unroll
+        for (int v = 0; v < VB; ++v) {
+            if (v0 + v < nvec) {
+                cpx<R> p[3];
+                VFmt<VPI>::template load<CGI>(ib + (int64_t)(v0 + v) * vs_in, g.Ps, fw[d], p);
+                mv_add(m, p, acc[v]);
+            }
+        }
+        WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, bw[d], m);
+#pragma unroll
+        for (int v = 0; v < VB; ++v) {
+            if (v0 + v < nvec) {
+                cpx<R> p[3];
+                VFmt<VPI>::template load<CGI>(ib + (int64_t)(v0 + v) * vs_in, g.Ps, bw[d], p);
+                mdv_add(m, p, acc[v]);
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+        if (v0 + v < nvec) {
+            cpx<R> c[3], o[3];
+            VFmt<VPI>::template load<CGI>(ib + (int64_t)(v0 + v) * vs_in, g.Ps, i, c);
+            const R a = (R)alpha[v0 + v];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                o[k].re = fma(a, fma(R(-6), c[k].re, acc[v][k].re), c[k].re);
+                o[k].im = fma(a, fma(R(-6), c[k].im, acc[v][k].im), c[k].im);
+            }
+            VFmt<VPO>::template store<CGO>(out + bout + (int64_t)(v0 + v) * vs_out, g.Ps, i, o);
+        }
+    }
+}
+
+// Work item w -> (site, chunk): warps own 32 consecutive sites, the nchunk
+// warps of one 32-site tile are consecutive.
+__device__ __forceinline__ void item_of(int64_t w, int nchunk, int64_t &site, int &chunk)
+{
+    int64_t tile = w / (32 * nchunk);
+    int r = (int)(w - tile * 32 * nchunk);
+    chunk = r >> 5;
+    site = tile * 32 + (r & 31);
+}
+
+template <int VP, int WF, int VB>
+__global__ void __launch_bounds__(256) k_step(const char *__restrict__ W, const char *__restrict__ in,
+                                              char *__restrict__ out, const double *__restrict__ alpha,
+                                              SubGeom g, int nblk, int nvec, int64_t vs_in, int64_t vs_out)
+{
+    const int nchunk = (nvec + VB - 1) / VB;
+    int64_t site;
+    int chunk;
+    item_of((int64_t)blockIdx.x * blockDim.x + threadIdx.x, nchunk, site, chunk);
+    if (site >= (int64_t)nblk * g.Vs) return;
+    const int blk = (int)(site / g.Vs);
+    const int i = (int)(site - (int64_t)blk * g.Vs);
+    constexpr int VBY = vfmt_bytes(VP);
+    const int64_t boff = (int64_t)blk * g.Ps * VBY;
+    site_step<VP, VP, WF, VB, false, false>(W, in, out, alpha, g, blk, i, chunk * VB, nvec, vs_in, vs_out, boff,
+                                            boff);
+}
+
+// --------------------------------------------------------------------------
+// Bounded grid barrier.  Generation-counting barrier over all co-resident CTAs
+// of a cooperative launch.  Every wait polls at most `budget` times; on
+// expiry the CTA sets DERR_TIMEOUT in *err and returns false, and every other
+// CTA stops waiting as soon as it sees that bit.  Nothing here can spin
+// forever.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_s32(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, long long budget)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (ld_relaxed_s32(err) & DERR_TIMEOUT) {
+            ok = 0;
+        } else {
+            unsigned *count = bar, *gen = bar + 1;
+            const unsigned g0 = ld_acquire_u32(gen);
+            __threadfence();
+            const unsigned arrived = atomicAdd(count, 1u);
+            if (arrived == gridDim.x - 1) {
+                atomicExch(count, 0u);
+                __threadfence();
+                atomicAdd(gen, 1u);
+            } else {
+                long long polls = 0;
+                while (ld_acquire_u32(gen) == g0) {
+                    if (++polls > budget || (ld_relaxed_s32(err) & DERR_TIMEOUT)) {
+                        atomicOr(err, DERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Persistent multi-step kernel: the (slice, sublattice) blocks are taken in
+// groups sized to stay resident in L2; each group runs all N steps before the
+// next group starts, with a grid barrier between steps.  Step 0 reads the
+// storage-precision input, steps 1..N-1 read the scratch ping-pong (SP
+// precision, L2-only loads), step N-1 writes the storage-precision output.
+template <int VP, int WF, int VB>
+__global__ void __launch_bounds__(256) k_persist(const char *__restrict__ W, const char *__restrict__ in,
+                                                 char *__restrict__ out, char *scr0, char *scr1,
+                                                 const double *__restrict__ alpha, SubGeom g, int nblk, int nvec,
+                                                 int N, int gb, int64_t vs, int64_t ss, unsigned *bar, int *err,
+                                                 long long budget)
+{
+    constexpr int SP = scratch_prec<VP>();
+    constexpr int VBY = vfmt_bytes(VP), SBY = vfmt_bytes(SP);
+    const int nchunk = (nvec + VB - 1) / VB;
+    const int ngroups = (nblk + gb - 1) / gb;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int grp = 0; grp < ngroups; ++grp) {
+        const int b0 = grp * gb;
+        const int nb = min(gb, nblk - b0);
+        const int64_t nsite = (int64_t)nb * g.Vs;
+        const int64_t items = ((nsite + 31) / 32) * 32 * nchunk;
+        for (int it = 0; it < N; ++it) {
+            const bool first = it == 0, last = it == N - 1;
+            const char *src = (it & 1) ? scr0 : scr1;  // scratch written by step it-1
+            char *dst = (it & 1) ? scr1 : scr0;
+            for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < items; w += stride) {
+                int64_t site;
+                int chunk;
+                item_of(w, nchunk, site, chunk);
+                if (site >= nsite) continue;
+                const int rb = (int)(site / g.Vs);
+                const int i = (int)(site - (int64_t)rb * g.Vs);
+                const int ab = b0 + rb;
+                const int64_t aoff = (int64_t)ab * g.Ps * VBY;  // absolute block in in/out
+                const int64_t soff = (int64_t)rb * g.Ps * SBY;  // group-relative block in scratch
+                if (first && last)
+                    site_step<VP, VP, WF, VB, false, false>(W, in, out, alpha, g, ab, i, chunk * VB, nvec, vs, vs,
+                                                            aoff, aoff);
+                else if (first)
+                    site_step<VP, SP, WF, VB, false, true>(W, in, dst, alpha, g, ab, i, chunk * VB, nvec, vs, ss,
+                                                           aoff, soff);
+                else if (last)
+                    site_step<SP, VP, WF, VB, true, false>(W, src, out, alpha, g, ab, i, chunk * VB, nvec, ss, vs,
+                                                           soff, aoff);
+                else
+                    site_step<SP, SP, WF, VB, true, true>(W, src, dst, alpha, g, ab, i, chunk * VB, nvec, ss, ss,
+                                                          soff, soff);
+            }
+            if (grp == ngroups - 1 && last) break;
+            if (!grid_barrier(bar, err, budget)) return;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Host-side launchers (per vector precision).
+// --------------------------------------------------------------------------
+template <int VP, int WF, int VB> cudaError_t step_launch(const StepArgs &a)
+{
+    const int nchunk = (a.nvec + VB - 1) / VB;
+    const int64_t nsite = (int64_t)a.nblk * a.g.Vs;
+    const int64_t items = ((nsite + 31) / 32) * 32 * nchunk;
+    const int threads = a.threads > 0 ? a.threads : 128;
+    const int64_t blocks = (items + threads - 1) / threads;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_step<VP, WF, VB><<<(unsigned)blocks, threads, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g, a.nblk, a.nvec,
+                                                                   a.vstride_in, a.vstride_out);
+    return cudaGetLastError();
+}
+
+template <int VP, int WF, int VB> cudaError_t persist_launch(const PersistArgs &a)
+{
+    void *args[] = {(void *)&a.W,  (void *)&a.in,   (void *)&a.out,    (void *)&a.scr[0], (void *)&a.scr[1],
+                    (void *)&a.alpha, (void *)&a.g, (void *)&a.nblk, (void *)&a.nvec,   (void *)&a.N,
+                    (void *)&a.group_blocks, (void *)&a.vstride, (void *)&a.sstride, (void *)&a.bar,
+                    (void *)&a.err, (void *)&a.budget};
+    return cudaLaunchCooperativeKernel((const void *)k_persist<VP, WF, VB>, dim3(a.grid), dim3(a.threads), args, 0,
+                                       a.stream);
+}
+
+template <int VP, int WF, int VB> int persist_occ(int threads)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<VP, WF, VB>, threads, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+template <int VP, int WF> cudaError_t step_w(const StepArgs &a)
+{
+    if constexpr (!combo_ok<VP, WF>()) {
+        return cudaErrorNotSupported;
+    } else {
+        switch (a.vb) {
+        case 1: return step_launch<VP, WF, 1>(a);
+        case 2: return step_launch<VP, WF, 2>(a);
+        case 4: return step_launch<VP, WF, 4>(a);
+        case 8:
+            if constexpr (VP != P_F64) return step_launch<VP, WF, 8>(a);
+            else return cudaErrorNotSupported;
+        default: return cudaErrorNotSupported;
+        }
+    }
+}
+
+template <int VP, int WF> cudaError_t persist_w(const PersistArgs &a)
+{
+    if constexpr (!combo_ok<VP, WF>()) {
+        return cudaErrorNotSupported;
+    } else {
+        switch (a.vb) {
+        case 1: return persist_launch<VP, WF, 1>(a);
+        case 4: return persist_launch<VP, WF, 4>(a);
+        case 8:
+            if constexpr (VP != P_F64) return persist_launch<VP, WF, 8>(a);
+            else return cudaErrorNotSupported;
+        default: return cudaErrorNotSupported;
+        }
+    }
+}
+
+template <int VP, int WF> int occ_w(int vb, int threads)
+{
+    if constexpr (!combo_ok<VP, WF>()) {
+        return 0;
+    } else {
+        switch (vb) {
+        case 1: return persist_occ<VP, WF, 1>(threads);
+        case 4: return persist_occ<VP, WF, 4>(threads);
+        case 8:
+            if constexpr (VP != P_F64) return persist_occ<VP, WF, 8>(threads);
+            else return 0;
+        default: return 0;
+        }
+    }
+}
+
+#define TLS_WFMT_SWITCH(FN, VP, ARG, FAIL)                 \
+    switch (wf) {                                          \
+    case W_F64_18: return FN<VP, W_F64_18> ARG;            \
+    case W_F32_18: return FN<VP, W_F32_18> ARG;            \
+    case W_F32_12: return FN<VP, W_F32_12> ARG;            \
+    case W_F32_8: return FN<VP, W_F32_8> ARG;              \
+    case W_F16_18: return FN<VP, W_F16_18> ARG;            \
+    case W_F16_12: return FN<VP, W_F16_12> ARG;            \
+    case W_BF16_18: return FN<VP, W_BF16_18> ARG;          \
+    case W_BF16_12: return FN<VP, W_BF16_12> ARG;          \
+    default: return FAIL;                                  \
+    }
+
+template <int VP> cudaError_t step_dispatch(const StepArgs &a)
+{
+    const int wf = a.wfmt;
+    TLS_WFMT_SWITCH(step_w, VP, (a), cudaErrorNotSupported)
+}
+
+template <int VP> cudaError_t persist_dispatch(const PersistArgs &a)
+{
+    const int wf = a.wfmt;
+    TLS_WFMT_SWITCH(persist_w, VP, (a), cudaErrorNotSupported)
+}
+
+template <int VP> int occ_dispatch(int wf, int vb, int threads)
+{
+    TLS_WFMT_SWITCH(occ_w, VP, (vb, threads), 0)
+}
+
+}  // namespace tls

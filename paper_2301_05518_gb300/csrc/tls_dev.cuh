@@ -1,0 +1,411 @@
+// tls_dev.cuh -- device-side data formats of the two-link smearing library.
+//
+// Sublattice layout.  The +-2 hops of the two-link Laplacian (Sec. 2,
+// Eq. tlLapl1) never change the parity of any coordinate, so every time slice
+// splits into 8 independent sublattices sub = (x&1) | (y&1)<<1 | (z&1)<<2.
+// Inside a sublattice the site (x, y, z) sits at x' = x>>1, y' = y>>1,
+// z' = z>>1, i = (z' * hy + y') * hx + x' with h = L/2, and a +-2 hop becomes
+// a +-1 step with period h: a unit-stride neighbour.  A (slice, sublattice)
+// pair is a "block"; block b = ts * 8 + sub.  Each block holds Vs = hx*hy*hz
+// sites and is stored with a plane stride Ps = Vs rounded up to 32, so every
+// plane starts on a 128-byte boundary.
+//
+// Within a block each field is structure-of-arrays: a per-site record is cut
+// into 16-byte words, and word j of all sites forms one plane (Ps entries),
+// followed by an 8- or 4-byte remainder plane.  A warp of 32 consecutive
+// sites then reads 512 contiguous bytes per 16-byte word.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tls_types.h"
+
+namespace tls {
+
+template <typename T> struct cpx {
+    T re, im;
+};
+
+// Loads and stores with an optional L2-only policy (.cg).  Data that other
+// CTAs rewrite during one launch (the persistent kernel's scratch) must not
+// be served from a stale L1 line, so it goes through ld.global.cg / st.global.cg.
+template <bool CG, typename T> __device__ __forceinline__ T vld(const T *p)
+{
+    if constexpr (CG)
+        return __ldcg(p);
+    else
+        return *p;
+}
+template <bool CG, typename T> __device__ __forceinline__ void vst(T *p, T v)
+{
+    if constexpr (CG)
+        __stcg(p, v);
+    else
+        *p = v;
+}
+
+template <typename T> __device__ __forceinline__ void cmac(cpx<T> &acc, cpx<T> a, cpx<T> b)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+
+// acc += conj(a) * b
+template <typename T> __device__ __forceinline__ void cmacc(cpx<T> &acc, cpx<T> a, cpx<T> b)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
+
+// out += m v  (m row-major 3x3)
+template <typename T> __device__ __forceinline__ void mv_add(const cpx<T> m[9], const cpx<T> v[3], cpx<T> out[3])
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cmac(out[r], m[r * 3 + k], v[k]);
+}
+
+// out += m^dag v
+template <typename T> __device__ __forceinline__ void mdv_add(const cpx<T> m[9], const cpx<T> v[3], cpx<T> out[3])
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cmacc(out[r], m[k * 3 + r], v[k]);
+}
+
+// Row 3 of an SU(3) matrix from rows 1 and 2: r2 = conj(r0 x r1).
+template <typename T> __device__ __forceinline__ void third_row(cpx<T> m[9])
+{
+    const cpx<T> *a = m, *b = m + 3;
+    cpx<T> c0, c1, c2;
+    c0.re = a[1].re * b[2].re - a[1].im * b[2].im - (a[2].re * b[1].re - a[2].im * b[1].im);
+    c0.im = a[1].re * b[2].im + a[1].im * b[2].re - (a[2].re * b[1].im + a[2].im * b[1].re);
+    c1.re = a[2].re * b[0].re - a[2].im * b[0].im - (a[0].re * b[2].re - a[0].im * b[2].im);
+    c1.im = a[2].re * b[0].im + a[2].im * b[0].re - (a[0].re * b[2].im + a[0].im * b[2].re);
+    c2.re = a[0].re * b[1].re - a[0].im * b[1].im - (a[1].re * b[0].re - a[1].im * b[0].im);
+    c2.im = a[0].re * b[1].im + a[0].im * b[1].re - (a[1].re * b[0].im + a[1].im * b[0].re);
+    m[6].re = c0.re; m[6].im = -c0.im;
+    m[7].re = c1.re; m[7].im = -c1.im;
+    m[8].re = c2.re; m[8].im = -c2.im;
+}
+
+// --------------------------------------------------------------------------
+// 16-bit helpers
+// --------------------------------------------------------------------------
+template <typename H> struct H2;
+template <> struct H2<__half> {
+    typedef __half2 t;
+    static __device__ __forceinline__ float2 to2(uint32_t u)
+    {
+        __half2 h = *reinterpret_cast<__half2 *>(&u);
+        return __half22float2(h);
+    }
+    static __device__ __forceinline__ uint32_t from2(float a, float b)
+    {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+    static __device__ __forceinline__ uint32_t from2d(double a, double b)
+    {
+        __half lo = __double2half(a), hi = __double2half(b);
+        return (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+    }
+};
+template <> struct H2<__nv_bfloat16> {
+    typedef __nv_bfloat162 t;
+    static __device__ __forceinline__ float2 to2(uint32_t u)
+    {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&u);
+        return __bfloat1622float2(h);
+    }
+    static __device__ __forceinline__ uint32_t from2(float a, float b)
+    {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+    static __device__ __forceinline__ uint32_t from2d(double a, double b)
+    {
+        __nv_bfloat16 lo = __double2bfloat16(a), hi = __double2bfloat16(b);
+        return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+    }
+};
+
+// --------------------------------------------------------------------------
+// W formats.  blk points at the (block, direction) record group: planes of
+// 16-byte words, Ps entries each, then the remainder plane.
+//   load(blk, Ps, i, m)    -> m[9] complex in the arithmetic type
+//   store(blk, Ps, i, w)   <- w[18] doubles (row-major, re/im), rounded RN
+// --------------------------------------------------------------------------
+template <int F> struct WFmt;
+
+template <> struct WFmt<W_F64_18> {
+    typedef double R;
+    static __device__ __forceinline__ void load(const char *blk, int64_t Ps, int i, cpx<double> m[9])
+    {
+        const double2 *p = reinterpret_cast<const double2 *>(blk);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            double2 v = p[k * Ps + i];
+            m[k].re = v.x;
+            m[k].im = v.y;
+        }
+    }
+    static __device__ __forceinline__ void store(char *blk, int64_t Ps, int i, const double w[18])
+    {
+        double2 *p = reinterpret_cast<double2 *>(blk);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) p[k * Ps + i] = make_double2(w[2 * k], w[2 * k + 1]);
+    }
+};
+
+template <> struct WFmt<W_F32_18> {
+    typedef float R;
+    static __device__ __forceinline__ void load(const char *blk, int64_t Ps, int i, cpx<float> m[9])
+    {
+        const float4 *q = reinterpret_cast<const float4 *>(blk);
+        const float2 *r = reinterpret_cast<const float2 *>(blk + 4 * Ps * 16);
+        float f[18];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float4 v = q[k * Ps + i];
+            f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+        }
+        float2 v = r[i];
+        f[16] = v.x; f[17] = v.y;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) { m[k].re = f[2 * k]; m[k].im = f[2 * k + 1]; }
+    }
+    static __device__ __forceinline__ void store(char *blk, int64_t Ps, int i, const double w[18])
+    {
+        float4 *q = reinterpret_cast<float4 *>(blk);
+        float2 *r = reinterpret_cast<float2 *>(blk + 4 * Ps * 16);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            q[k * Ps + i] = make_float4(__double2float_rn(w[4 * k]), __double2float_rn(w[4 * k + 1]),
+                                        __double2float_rn(w[4 * k + 2]), __double2float_rn(w[4 * k + 3]));
+        r[i] = make_float2(__double2float_rn(w[16]), __double2float_rn(w[17]));
+    }
+};
+
+template <> struct WFmt<W_F32_12> {
+    typedef float R;
+    static __device__ __forceinline__ void load(const char *blk, int64_t Ps, int i, cpx<float> m[9])
+    {
+        const float4 *q = reinterpret_cast<const float4 *>(blk);
+        float f[12];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float4 v = q[k * Ps + i];
+            f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) { m[k].re = f[2 * k]; m[k].im = f[2 * k + 1]; }
+        third_row(m);
+    }
+    static __device__ __forceinline__ void store(char *blk, int64_t Ps, int i, const double w[18])
+    {
+        float4 *q = reinterpret_cast<float4 *>(blk);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            q[k * Ps + i] = make_float4(__double2float_rn(w[4 * k]), __double2float_rn(w[4 * k + 1]),
+                                        __double2float_rn(w[4 * k + 2]), __double2float_rn(w[4 * k + 3]));
+    }
+};
+
+// 8 reals: W01, W02, W10 (complex) and the phases of W00 and W20.  With
+// row 0 known up to |W00| and column 0 known up to |W20|:
+//   |W00|^2 = 1 - |W01|^2 - |W02|^2,   |W20|^2 = 1 - |W00|^2 - |W10|^2,
+// and, with n = |W01|^2 + |W02|^2 = 1 - |W00|^2 > 0, unitarity of row 1
+// against row 0 plus W20 = conj(W01 W12 - W02 W11) (row 2 = conj(r0 x r1))
+// give the 2x2 linear system solved by
+//   W11 = -(W10 conj(W00) W01 + conj(W02) conj(W20)) / n
+//   W12 =  (conj(W01) conj(W20) - W10 conj(W00) W02) / n
+// and row 2 follows as conj(r0 x r1).
+template <> struct WFmt<W_F32_8> {
+    typedef float R;
+    static __device__ __forceinline__ void load(const char *blk, int64_t Ps, int i, cpx<float> m[9])
+    {
+        const float4 *q = reinterpret_cast<const float4 *>(blk);
+        float4 a = q[i], b = q[Ps + i];
+        cpx<float> w01 = {a.x, a.y}, w02 = {a.z, a.w}, w10 = {b.x, b.y};
+        float n = w01.re * w01.re + w01.im * w01.im + w02.re * w02.re + w02.im * w02.im;
+        float a00 = sqrtf(fmaxf(1.0f - n, 0.0f));
+        float a20 = sqrtf(fmaxf(n - (w10.re * w10.re + w10.im * w10.im), 0.0f));
+        float s0, c0, s2, c2;
+        sincosf(b.z, &s0, &c0);
+        sincosf(b.w, &s2, &c2);
+        cpx<float> w00 = {a00 * c0, a00 * s0}, w20 = {a20 * c2, a20 * s2};
+        float inv = 1.0f / n;
+        // t = W10 conj(W00)
+        cpx<float> t = {w10.re * w00.re + w10.im * w00.im, w10.im * w00.re - w10.re * w00.im};
+        cpx<float> w11, w12;
+        // W11 = -(t W01 + conj(W02) conj(W20)) / n
+        w11.re = -((t.re * w01.re - t.im * w01.im) + (w02.re * w20.re - w02.im * w20.im)) * inv;
+        w11.im = -((t.re * w01.im + t.im * w01.re) - (w02.re * w20.im + w02.im * w20.re)) * inv;
+        // W12 = (conj(W01) conj(W20) - t W02) / n
+        w12.re = ((w01.re * w20.re - w01.im * w20.im) - (t.re * w02.re - t.im * w02.im)) * inv;
+        w12.im = (-(w01.re * w20.im + w01.im * w20.re) - (t.re * w02.im + t.im * w02.re)) * inv;
+        m[0] = w00; m[1] = w01; m[2] = w02;
+        m[3] = w10; m[4] = w11; m[5] = w12;
+        third_row(m);
+    }
+    // Returns false when |W00| is too close to 1 for the parameterisation.
+    static __device__ __forceinline__ bool store(char *blk, int64_t Ps, int i, const double w[18])
+    {
+        float4 *q = reinterpret_cast<float4 *>(blk);
+        double th0 = atan2(w[1], w[0]);
+        double th2 = atan2(w[13], w[12]);
+        q[i] = make_float4(__double2float_rn(w[2]), __double2float_rn(w[3]), __double2float_rn(w[4]),
+                           __double2float_rn(w[5]));
+        q[Ps + i] = make_float4(__double2float_rn(w[6]), __double2float_rn(w[7]), __double2float_rn(th0),
+                                __double2float_rn(th2));
+        double n = w[2] * w[2] + w[3] * w[3] + w[4] * w[4] + w[5] * w[5];
+        return n > 1e-6;
+    }
+};
+
+template <typename H, int NR> struct WFmtH {
+    // NR = 18 or 12 reals stored as 16-bit: 2 or 1 full 16-byte words + remainder.
+    typedef float R;
+    static constexpr int NQ = (NR * 2) / 16;
+    static constexpr int REM = (NR * 2) % 16;  // 4 or 8
+    static __device__ __forceinline__ void load(const char *blk, int64_t Ps, int i, cpx<float> m[9])
+    {
+        const uint4 *q = reinterpret_cast<const uint4 *>(blk);
+        uint32_t u[NR / 2];
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            uint4 v = q[k * Ps + i];
+            u[4 * k] = v.x; u[4 * k + 1] = v.y; u[4 * k + 2] = v.z; u[4 * k + 3] = v.w;
+        }
+        if constexpr (REM == 8) {
+            uint2 v = reinterpret_cast<const uint2 *>(blk + NQ * Ps * 16)[i];
+            u[4 * NQ] = v.x; u[4 * NQ + 1] = v.y;
+        } else {
+            u[4 * NQ] = reinterpret_cast<const uint32_t *>(blk + NQ * Ps * 16)[i];
+        }
+#pragma unroll
+        for (int k = 0; k < NR / 2; ++k) {
+            float2 f = H2<H>::to2(u[k]);
+            m[k].re = f.x;
+            m[k].im = f.y;
+        }
+        if constexpr (NR == 12) third_row(m);
+    }
+    static __device__ __forceinline__ void store(char *blk, int64_t Ps, int i, const double w[18])
+    {
+        uint32_t u[NR / 2];
+#pragma unroll
+        for (int k = 0; k < NR / 2; ++k) u[k] = H2<H>::from2d(w[2 * k], w[2 * k + 1]);
+        uint4 *q = reinterpret_cast<uint4 *>(blk);
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) q[k * Ps + i] = make_uint4(u[4 * k], u[4 * k + 1], u[4 * k + 2], u[4 * k + 3]);
+        if constexpr (REM == 8)
+            reinterpret_cast<uint2 *>(blk + NQ * Ps * 16)[i] = make_uint2(u[4 * NQ], u[4 * NQ + 1]);
+        else
+            reinterpret_cast<uint32_t *>(blk + NQ * Ps * 16)[i] = u[4 * NQ];
+    }
+};
+template <> struct WFmt<W_F16_18> : WFmtH<__half, 18> {};
+template <> struct WFmt<W_F16_12> : WFmtH<__half, 12> {};
+template <> struct WFmt<W_BF16_18> : WFmtH<__nv_bfloat16, 18> {};
+template <> struct WFmt<W_BF16_12> : WFmtH<__nv_bfloat16, 12> {};
+
+// --------------------------------------------------------------------------
+// Vector formats.  blk points at one (vector, block); site i.
+//   F64 : 3 planes of double2 (one complex colour component each)
+//   F32 : plane of float4 (colours 0, 1) + plane of float2 (colour 2)
+//   F16 / BF16 : one plane of 16-byte records {3 x (re, im) 16-bit, float s};
+//         the value is the stored number times s, s = max |re|, |im| of the
+//         site (s = 0 stores zeros).
+// --------------------------------------------------------------------------
+template <int P> struct VFmt;
+
+template <> struct VFmt<P_F64> {
+    typedef double R;
+    template <bool CG> static __device__ __forceinline__ void load(const char *blk, int64_t Ps, int i, cpx<double> v[3])
+    {
+        const double2 *p = reinterpret_cast<const double2 *>(blk);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double2 a = vld<CG>(p + c * Ps + i);
+            v[c].re = a.x;
+            v[c].im = a.y;
+        }
+    }
+    template <bool CG> static __device__ __forceinline__ void store(char *blk, int64_t Ps, int i, const cpx<double> v[3])
+    {
+        double2 *p = reinterpret_cast<double2 *>(blk);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vst<CG>(p + c * Ps + i, make_double2(v[c].re, v[c].im));
+    }
+};
+
+template <> struct VFmt<P_F32> {
+    typedef float R;
+    template <bool CG> static __device__ __forceinline__ void load(const char *blk, int64_t Ps, int i, cpx<float> v[3])
+    {
+        float4 a = vld<CG>(reinterpret_cast<const float4 *>(blk) + i);
+        float2 b = vld<CG>(reinterpret_cast<const float2 *>(blk + Ps * 16) + i);
+        v[0].re = a.x; v[0].im = a.y; v[1].re = a.z; v[1].im = a.w; v[2].re = b.x; v[2].im = b.y;
+    }
+    template <bool CG> static __device__ __forceinline__ void store(char *blk, int64_t Ps, int i, const cpx<float> v[3])
+    {
+        vst<CG>(reinterpret_cast<float4 *>(blk) + i, make_float4(v[0].re, v[0].im, v[1].re, v[1].im));
+        vst<CG>(reinterpret_cast<float2 *>(blk + Ps * 16) + i, make_float2(v[2].re, v[2].im));
+    }
+};
+
+template <typename H> struct VFmtH {
+    typedef float R;
+    template <bool CG> static __device__ __forceinline__ void load(const char *blk, int64_t, int i, cpx<float> v[3])
+    {
+        uint4 a = vld<CG>(reinterpret_cast<const uint4 *>(blk) + i);
+        float s = __uint_as_float(a.w);
+        float2 f0 = H2<H>::to2(a.x), f1 = H2<H>::to2(a.y), f2 = H2<H>::to2(a.z);
+        v[0].re = f0.x * s; v[0].im = f0.y * s;
+        v[1].re = f1.x * s; v[1].im = f1.y * s;
+        v[2].re = f2.x * s; v[2].im = f2.y * s;
+    }
+    template <bool CG> static __device__ __forceinline__ void store(char *blk, int64_t, int i, const cpx<float> v[3])
+    {
+        float m = fmaxf(fmaxf(fmaxf(fabsf(v[0].re), fabsf(v[0].im)), fmaxf(fabsf(v[1].re), fabsf(v[1].im))),
+                        fmaxf(fabsf(v[2].re), fabsf(v[2].im)));
+        float inv = m > 0.0f ? 1.0f / m : 0.0f;
+        uint4 a;
+        a.x = H2<H>::from2(v[0].re * inv, v[0].im * inv);
+        a.y = H2<H>::from2(v[1].re * inv, v[1].im * inv);
+        a.z = H2<H>::from2(v[2].re * inv, v[2].im * inv);
+        a.w = __float_as_uint(m);
+        vst<CG>(reinterpret_cast<uint4 *>(blk) + i, a);
+    }
+};
+template <> struct VFmt<P_F16> : VFmtH<__half> {};
+template <> struct VFmt<P_BF16> : VFmtH<__nv_bfloat16> {};
+
+// The six +-1 sublattice neighbours of site i (periodic in h).
+__device__ __forceinline__ void sub_neighbours(const SubGeom &g, int i, int fw[3], int bw[3])
+{
+    int xq = i % g.hx;
+    int r = i / g.hx;
+    int yq = r % g.hy;
+    int zq = r / g.hy;
+    int sy = g.hx, sz = g.hx * g.hy;
+    fw[0] = xq == g.hx - 1 ? i - (g.hx - 1) : i + 1;
+    bw[0] = xq == 0 ? i + (g.hx - 1) : i - 1;
+    fw[1] = yq == g.hy - 1 ? i - (g.hy - 1) * sy : i + sy;
+    bw[1] = yq == 0 ? i + (g.hy - 1) * sy : i - sy;
+    fw[2] = zq == g.hz - 1 ? i - (g.hz - 1) * sz : i + sz;
+    bw[2] = zq == 0 ? i + (g.hz - 1) * sz : i - sz;
+}
+
+}  // namespace tls

@@ -1,0 +1,89 @@
+// tls_internal.h -- host-side launch interface between the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tls_types.h"
+
+namespace tls {
+
+// One smearing-step launch over nblk (slice, sublattice) blocks and nvec vectors.
+struct StepArgs {
+    const char *W;         // W of the first selected block
+    const char *in;        // packed vectors: vector v at in + v * vstride_in
+    char *out;
+    const double *alpha;   // device, per vector: width / (4 N)
+    SubGeom g;
+    int nblk;
+    int nvec;
+    int64_t vstride_in;    // bytes between vectors
+    int64_t vstride_out;
+    int wfmt;
+    int prec_in;           // vector storage of `in`
+    int prec_out;          // vector storage of `out`
+    int vb;                // vectors per thread
+    int threads;           // threads per CTA (multiple of 32)
+    cudaStream_t stream;
+};
+
+// Persistent multi-step launch: all N steps, group by group.
+struct PersistArgs {
+    const char *W;
+    const char *in;        // storage prec (read at step 0)
+    char *out;             // storage prec (written at step N-1)
+    char *scr[2];          // scratch ping-pong, scratch prec, sized for one group
+    const double *alpha;
+    SubGeom g;
+    int nblk, nvec, N;
+    int group_blocks;      // blocks per group
+    int64_t vstride;       // bytes between vectors of in/out
+    int64_t sstride;       // bytes between vectors of scratch
+    int wfmt, prec, sprec, vb, threads;
+    unsigned *bar;         // 2 words: arrival count, generation (zeroed)
+    int *err;              // device error word
+    long long budget;      // polls per barrier
+    int grid;              // CTAs (co-resident)
+    cudaStream_t stream;
+};
+
+// Returns cudaErrorNotSupported for combinations without a kernel.
+cudaError_t launch_step(const StepArgs &a);
+cudaError_t launch_persistent(const PersistArgs &a);
+// Co-resident CTAs per SM of the persistent kernel for this combination (0: none).
+int persistent_occupancy(int wfmt, int prec, int sprec, int vb, int threads);
+
+// Per-precision entry points (one translation unit each).
+cudaError_t launch_step_f64(const StepArgs &a);
+cudaError_t launch_step_f32(const StepArgs &a);
+cudaError_t launch_step_f16(const StepArgs &a);
+cudaError_t launch_step_bf16(const StepArgs &a);
+cudaError_t launch_persistent_f64(const PersistArgs &a);
+cudaError_t launch_persistent_f32(const PersistArgs &a);
+cudaError_t launch_persistent_f16(const PersistArgs &a);
+cudaError_t launch_persistent_bf16(const PersistArgs &a);
+int persistent_occupancy_f64(int wfmt, int vb, int threads);
+int persistent_occupancy_f32(int wfmt, int vb, int threads);
+int persistent_occupancy_f16(int wfmt, int vb, int threads);
+int persistent_occupancy_bf16(int wfmt, int vb, int threads);
+
+// Layout kernels (k_layout.cu).
+cudaError_t launch_ingest_gauge(const double *U, int nd, double *Up, const SubGeom &g, const int L[4],
+                                cudaStream_t s);
+cudaError_t launch_export_gauge(const double *Up, double *out, const SubGeom &g, const int L[4], cudaStream_t s);
+cudaError_t launch_build_twolink(const double *Up, char *W, int wfmt, const SubGeom &g, int nblk, int *err,
+                                 cudaStream_t s);
+cudaError_t launch_export_twolink(const char *W, int wfmt, double *out, const SubGeom &g, const int L[4],
+                                  cudaStream_t s);
+// Canonical caller vectors (io_prec F64/F32, slices [t_first, t_first + nsl)) -> packed storage.
+cudaError_t launch_pack_vectors(const void *src, int io_prec, int64_t src_vstride_sites, char *dst, int prec,
+                                int64_t dst_vstride, const SubGeom &g, const int L[4], int t_first, int nsl,
+                                int nvec, cudaStream_t s);
+// Packed storage -> canonical; partials (nullable) gets one FP64 sum of |psi|^2 per (vector, CTA).
+cudaError_t launch_unpack_vectors(const char *src, int prec, int64_t src_vstride, void *dst, int io_prec,
+                                  int64_t dst_vstride_sites, const SubGeom &g, const int L[4], int t_first,
+                                  int nsl, int nvec, double *partials, int *nparts, cudaStream_t s);
+cudaError_t launch_reduce_norms(const double *partials, int nparts, int nvec, double *norms, cudaStream_t s);
+int unpack_parts(const SubGeom &g, int nsl);
+
+}  // namespace tls

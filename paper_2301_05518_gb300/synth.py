@@ -83,7 +83,7 @@ def reunitarize(m: torch.Tensor) -> torch.Tensor:
     return torch.stack([r1, r2, r3], dim=-2)
 
 
-def _expm_taylor(x: torch.Tensor, order: int = 24) -> torch.Tensor:
+def _expm_taylor(x: torch.Tensor, order: int = 18) -> torch.Tensor:
     """exp(x) for [..., 3, 3] by a Horner-form Taylor series (small ||x||)."""
     eye = torch.eye(3, dtype=x.dtype, device=x.device).expand_as(x)
     e = eye.clone()

@@ -1,0 +1,340 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (relative L2 per vector against the FP64 oracle):
+  FP64 storage        <= 1e-13
+  FP32 storage        <= 2e-6 * N   (raw error / N <= 2e-6)
+  FP16/BF16 storage   <= 5e-3
+Index maps (ingest, sublattice decoupling, untouched slices) are bit-exact.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import per_vector_rel_l2, rel_l2, sublattice_mask
+from paper_2301_05518_gb300 import synth, workloads
+
+pytestmark = pytest.mark.gpu
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2301_05518_gb300 import tls as t
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    c = T.Context(0)
+    yield c
+    c.close()
+
+
+def tol(storage, N):
+    from paper_2301_05518_gb300 import tls as t
+    if storage == t.TLS_F64:
+        return 1e-13
+    if storage == t.TLS_F32:
+        return 2e-6 * max(N, 1)
+    return 5e-3
+
+
+def gauge_dev(dims, kind, seed, eps=0.3, nd=4):
+    if kind == "haar":
+        return synth.gauge_haar(dims, seed, nd=nd, device="cuda")
+    return synth.gauge_near_unit(dims, eps, seed, nd=nd, device="cuda")
+
+
+_ORACLE_CACHE = {}
+
+
+def cached(key, fn):
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = fn()
+    return _ORACLE_CACHE[key]
+
+
+def gauge(dims, kind, seed, eps=0.3, nd=4):
+    if kind == "haar":
+        return synth.gauge_haar(dims, seed, nd=nd)
+    if kind == "unit":
+        return synth.gauge_unit(dims, nd=nd)
+    return synth.gauge_near_unit(dims, eps, seed, nd=nd)
+
+
+# ------------------------------------------------------------------ ingest
+@pytest.mark.parametrize("dims", [(4, 6, 8, 3), (2, 2, 2, 1), (6, 10, 4, 2), (8, 8, 8, 2)])
+@pytest.mark.parametrize("nd,on_device", [(4, False), (3, True)])
+def test_ingest_roundtrip_bit_exact(ctx, T, dims, nd, on_device):
+    U = gauge(dims, "haar", 5, nd=nd)
+    src = U.cuda() if on_device else U
+    gid = ctx.load_gauge(src, nd, dims)
+    out = np.zeros(U.shape[:4] + (3, 3, 3), dtype=np.complex128)
+    ctx.export_gauge(gid, out)
+    assert np.array_equal(out, U.numpy()[..., :3, :, :])
+    ctx.free_gauge(gid)
+
+
+# ------------------------------------------------------------------ build
+BUILD_CASES = [("F64", 18, 1e-15), ("F32", 18, 4e-7), ("F32", 12, 1e-6), ("F32", 8, 3e-6),
+               ("F16", 18, 6e-4), ("F16", 12, 2e-3), ("BF16", 18, 5e-3), ("BF16", 12, 1.5e-2)]
+
+
+@pytest.mark.parametrize("prec,recon,bound", BUILD_CASES)
+def test_build_matches_oracle(ctx, T, prec, recon, bound):
+    dims = (6, 4, 8, 3)
+    U = gauge(dims, "haar", 7)
+    want = oracle.twolink(U.numpy())
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.build_twolink(gid, getattr(T, "TLS_" + prec), recon)
+    got = np.zeros_like(want)
+    ctx.export_twolink(gid, got)
+    assert np.abs(got - want).max() <= bound
+    ctx.free_gauge(gid)
+
+
+def test_build_recon8_rejects_identity(ctx, T):
+    dims = (4, 4, 4, 1)
+    gid = ctx.load_gauge(gauge(dims, "unit", 0), 4, dims)
+    with pytest.raises(T.TLSError) as e:
+        ctx.build_twolink(gid, T.TLS_F32, T.TLS_R8)
+    assert e.value.status == T.TLS_ERR_DEVICE
+    ctx.build_twolink(gid, T.TLS_F32, T.TLS_R12)  # the context stays usable
+    ctx.free_gauge(gid)
+
+
+# ------------------------------------------------------------------ smearing parity
+def _run(ctx, T, U, dims, vecs, storage, wprec, recon, kernel, N, sigma, t0, io=None, host=False):
+    gid = ctx.load_gauge(U, U.shape[4], dims)
+    ctx.build_twolink(gid, wprec, recon)
+    io = io if io is not None else (T.TLS_F64 if storage == T.TLS_F64 else T.TLS_F32)
+    dt = torch.complex128 if io == T.TLS_F64 else torch.complex64
+    x = vecs.to(dt).contiguous()
+    x = x if host else x.cuda()
+    norms = ctx.smear(gid, x, io, x.shape[0], N, sigma, timeslice=t0, storage=storage, kernel=kernel,
+                      norms=True)
+    ctx.free_gauge(gid)
+    return x.cpu().numpy().astype(np.complex128), norms
+
+
+SMEAR_CASES = [
+    # storage, W prec, recon, kernels
+    ("F64", "F64", 18, ("SINGLE", "MRHS", "PERSISTENT")),
+    ("F32", "F32", 18, ("SINGLE", "MRHS", "PERSISTENT")),
+    ("F32", "F32", 12, ("MRHS", "PERSISTENT")),
+    ("F32", "F32", 8, ("MRHS", "PERSISTENT")),
+    ("F16", "F32", 18, ("MRHS", "PERSISTENT")),
+    ("F16", "F16", 12, ("MRHS", "PERSISTENT")),
+    ("F16", "F16", 18, ("SINGLE",)),
+    ("BF16", "F32", 12, ("MRHS", "PERSISTENT")),
+    ("BF16", "BF16", 18, ("MRHS",)),
+]
+
+
+@pytest.mark.parametrize("storage,wprec,recon,kernels", SMEAR_CASES)
+@pytest.mark.parametrize("t0", [-1, 1])
+def test_smear_matches_oracle(ctx, T, storage, wprec, recon, kernels, t0):
+    dims = (6, 4, 8, 3)
+    U = gauge(dims, "haar", 11)
+    vecs = synth.gaussian_vectors(dims, 5, 12)
+    N, sigma = 7, 1.4
+    want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy(), N, sigma, t0=t0)
+    st = getattr(T, "TLS_" + storage)
+    for kname in kernels:
+        got, norms = _run(ctx, T, U, dims, vecs, st, getattr(T, "TLS_" + wprec), recon,
+                          getattr(T, "TLS_KERNEL_" + kname), N, sigma, t0)
+        errs = per_vector_rel_l2(got, want)
+        assert max(errs) <= tol(st, N), (kname, errs)
+        # untouched slices are bit-exact copies (within the io precision)
+        if t0 >= 0:
+            io_in = vecs.numpy() if st == T.TLS_F64 else vecs.to(torch.complex64).numpy().astype(np.complex128)
+            for t in range(dims[3]):
+                if t != t0:
+                    assert np.array_equal(got[:, t], io_in[:, t])
+        sl = slice(None) if t0 < 0 else slice(t0, t0 + 1)
+        ref_norms = (np.abs(got[:, sl]) ** 2).reshape(got.shape[0], -1).sum(1)
+        assert np.allclose(norms, ref_norms, rtol=1e-12, atol=0)
+
+
+def test_io_f64_with_f32_storage(ctx, T):
+    dims = (4, 4, 6, 2)
+    U = gauge(dims, "near", 13)
+    vecs = synth.gaussian_vectors(dims, 3, 14)
+    N, sigma = 5, 1.0
+    want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy(), N, sigma)
+    got, _ = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 18, T.TLS_KERNEL_MRHS, N, sigma, -1,
+                  io=T.TLS_F64)
+    assert max(per_vector_rel_l2(got, want)) <= 2e-6 * N
+
+
+@pytest.mark.parametrize("storage", ["F64", "F32", "F16"])
+def test_mrhs_bitwise_equals_single_vector(ctx, T, storage):
+    """A vector's result does not depend on nvec or on the other vectors in the batch."""
+    dims = (8, 4, 6, 2)
+    U = gauge(dims, "haar", 15)
+    vecs = synth.gaussian_vectors(dims, 6, 16)
+    st = getattr(T, "TLS_" + storage)
+    wp = T.TLS_F64 if st == T.TLS_F64 else T.TLS_F32
+    batch, _ = _run(ctx, T, U, dims, vecs, st, wp, 18, T.TLS_KERNEL_MRHS, 6, 1.3, -1)
+    single, _ = _run(ctx, T, U, dims, vecs, st, wp, 18, T.TLS_KERNEL_SINGLE, 6, 1.3, -1)
+    assert np.array_equal(batch, single)
+    alone, _ = _run(ctx, T, U, dims, vecs[3:4], st, wp, 18, T.TLS_KERNEL_MRHS, 6, 1.3, -1)
+    assert np.array_equal(alone[0], batch[3])
+    p_batch, _ = _run(ctx, T, U, dims, vecs, st, wp, 18, T.TLS_KERNEL_PERSISTENT, 6, 1.3, -1)
+    p_alone, _ = _run(ctx, T, U, dims, vecs[2:3], st, wp, 18, T.TLS_KERNEL_PERSISTENT, 6, 1.3, -1)
+    assert np.array_equal(p_alone[0], p_batch[2])
+
+
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+def test_zero_steps_and_zero_width_are_identity(ctx, T, storage):
+    dims = (4, 4, 4, 2)
+    U = gauge(dims, "haar", 17)
+    vecs = synth.gaussian_vectors(dims, 2, 18)
+    st = getattr(T, "TLS_" + storage)
+    wp = T.TLS_F64 if st == T.TLS_F64 else T.TLS_F32
+    ref = vecs.numpy() if st == T.TLS_F64 else vecs.to(torch.complex64).numpy().astype(np.complex128)
+    for kern in (T.TLS_KERNEL_MRHS, T.TLS_KERNEL_PERSISTENT):
+        got, _ = _run(ctx, T, U, dims, vecs, st, wp, 18, kern, 0, 2.0, -1)
+        assert np.array_equal(got, ref)
+        got, _ = _run(ctx, T, U, dims, vecs, st, wp, 18, kern, 4, 0.0, -1)
+        assert np.array_equal(got, ref)
+
+
+def test_host_buffers_match_device(ctx, T):
+    dims = (6, 6, 4, 3)
+    U = gauge(dims, "near", 19)
+    vecs = synth.gaussian_vectors(dims, 3, 20)
+    for t0 in (-1, 2):
+        dev, _ = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 18, T.TLS_KERNEL_MRHS, 5, 1.0, t0)
+        host, _ = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 18, T.TLS_KERNEL_MRHS, 5, 1.0, t0,
+                       host=True)
+        assert np.array_equal(dev, host)
+
+
+def test_two_site_extent(ctx, T):
+    """L = 2 in every direction: the hop returns to the same site through W and W^dag."""
+    dims = (2, 2, 2, 2)
+    U = gauge(dims, "haar", 21)
+    vecs = synth.gaussian_vectors(dims, 2, 22)
+    want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy(), 5, 1.5)
+    for kern in (T.TLS_KERNEL_MRHS, T.TLS_KERNEL_PERSISTENT):
+        got, _ = _run(ctx, T, U, dims, vecs, T.TLS_F64, T.TLS_F64, 18, kern, 5, 1.5, -1)
+        assert rel_l2(got, want) <= 1e-13
+
+
+# ------------------------------------------------------------------ errors
+def test_error_paths(ctx, T):
+    dims = (4, 4, 4, 2)
+    U = gauge(dims, "haar", 23)
+    with pytest.raises(T.TLSError) as e:
+        ctx.load_gauge(U[:, :, :, :3].contiguous(), 4, (3, 4, 4, 2))
+    assert e.value.status == T.TLS_ERR_ARG
+    gid = ctx.load_gauge(U, 4, dims)
+    x = synth.gaussian_vectors(dims, 1, 1).to(torch.complex64).cuda()
+    with pytest.raises(T.TLSError) as e:
+        ctx.smear(gid, x, T.TLS_F32, 1, 3, 1.0)
+    assert e.value.status == T.TLS_ERR_NOT_BUILT
+    ctx.build_twolink(gid, T.TLS_F32, 18)
+    for kwargs, code in [(dict(N=-1), T.TLS_ERR_ARG), (dict(timeslice=2), T.TLS_ERR_ARG),
+                         (dict(storage=T.TLS_F64), T.TLS_ERR_UNSUPPORTED)]:
+        args = dict(N=3, timeslice=-1, storage=T.TLS_F32)
+        args.update(kwargs)
+        with pytest.raises(T.TLSError) as e:
+            ctx.smear(gid, x, T.TLS_F32, 1, args["N"], 1.0, timeslice=args["timeslice"],
+                      storage=args["storage"])
+        assert e.value.status == code
+    ctx.free_gauge(gid)
+    with pytest.raises(T.TLSError) as e:
+        ctx.smear(gid, x, T.TLS_F32, 1, 3, 1.0)
+    assert e.value.status == T.TLS_ERR_NOT_FOUND
+
+
+def test_hbm_cap_admission(T):
+    dims = (8, 8, 8, 4)
+    with T.Context(0, hbm_cap_bytes=8 << 20) as c:
+        U = gauge(dims, "haar", 24)
+        gid = c.load_gauge(U, 4, dims)          # 8^3*4 * 3 * 144 B = 884 KB
+        c.build_twolink(gid, T.TLS_F32, 18)
+        x = synth.gaussian_vectors(dims, 200, 2).to(torch.complex64).cuda()  # ~ 2 x 9.8 MB packed
+        with pytest.raises(T.TLSError) as e:
+            c.smear(gid, x, T.TLS_F32, 200, 2, 1.0)
+        assert e.value.status == T.TLS_ERR_ADMIT
+        assert c.bytes_in_use() <= 8 << 20
+        c.smear(gid, x[:2].contiguous(), T.TLS_F32, 2, 2, 1.0)  # still usable
+
+
+def test_barrier_timeout_returns_status(ctx, T):
+    """A barrier budget of one poll makes the waits run out; the context stays usable."""
+    dims = (16, 16, 16, 2)
+    U = gauge(dims, "near", 25)
+    vecs = synth.gaussian_vectors(dims, 1, 26)
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.build_twolink(gid, T.TLS_F32, 18)
+    x = vecs.to(torch.complex64).cuda()
+    ctx.set_barrier_budget(1)
+    try:
+        with pytest.raises(T.TLSError) as e:
+            ctx.smear(gid, x, T.TLS_F32, 1, 20, 4.0, kernel=T.TLS_KERNEL_PERSISTENT)
+        assert e.value.status == T.TLS_ERR_TIMEOUT
+    finally:
+        ctx.set_barrier_budget(0)
+    x = vecs.to(torch.complex64).cuda()
+    ctx.smear(gid, x, T.TLS_F32, 1, 20, 4.0, kernel=T.TLS_KERNEL_PERSISTENT)
+    want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy(), 20, 4.0)
+    assert rel_l2(x.cpu().numpy().astype(np.complex128), want) <= 2e-6 * 20
+    ctx.free_gauge(gid)
+
+
+# ------------------------------------------------------------------ the named workloads
+def test_small_point_source_workload(ctx, T):
+    w = workloads.SMALL_POINT
+    dims = w["dims"]
+    U = gauge(dims, "near", w["gauge_seed"], eps=w["eps"])
+    psi = synth.point_sources(dims, [(0, 0, 0, 0)], [0])
+    want = oracle.smear(oracle.twolink(U.numpy()), psi.numpy(), w["N"], w["sigma"], t0=w["timeslice"])
+    for kern in (T.TLS_KERNEL_SINGLE, T.TLS_KERNEL_MRHS, T.TLS_KERNEL_PERSISTENT):
+        got, _ = _run(ctx, T, U, dims, psi, T.TLS_F64, T.TLS_F64, 18, kern, w["N"], w["sigma"],
+                      w["timeslice"])
+        assert rel_l2(got, want) <= 1e-13
+        assert np.all(got[0, 1:] == 0)
+        mask = sublattice_mask(dims, 0)
+        assert np.all(got[0, 0][~mask] == 0)
+
+
+@pytest.mark.parametrize("storage", ["F64", "F32"])
+def test_medium_mixed_workload(ctx, T, storage):
+    w = workloads.MEDIUM_MIXED
+    dims = w["dims"]
+    U = cached("medium_U", lambda: gauge_dev(dims, "near", w["gauge_seed"], eps=w["eps"]).cpu())
+    pts = synth.point_sources(dims, [(0, 0, 0, 0)] * 3, [0, 1, 2])
+    gs = synth.gaussian_vectors(dims, 3, w["vec_seed"])
+    def ref():
+        W = oracle.twolink(U.numpy())
+        return np.concatenate([oracle.smear(W, pts.numpy(), w["N"], w["sigma"], t0=0),
+                               oracle.smear(W, gs.numpy(), w["N"], w["sigma"])])
+    want = cached("medium", ref)
+    st = getattr(T, "TLS_" + storage)
+    got, _ = _run(ctx, T, U, dims, torch.cat([pts, gs]), st, st, 18, T.TLS_KERNEL_SINGLE, w["N"],
+                  w["sigma"], -1)
+    errs = per_vector_rel_l2(got, want)
+    assert max(errs) <= tol(st, w["N"]), errs
+
+
+@pytest.mark.parametrize("storage,wprec,recon", [("F32", "F32", 18), ("F32", "F32", 8),
+                                                 ("F16", "F16", 12), ("BF16", "F32", 12)])
+def test_large_mrhs_workload_sampled(ctx, T, storage, wprec, recon):
+    """48^3x64 Haar, a batch of 12 on the device, checked on two sampled (vector, slice) pairs."""
+    w = workloads.LARGE_MRHS
+    dims = w["dims"]
+    U = gauge_dev(dims, "haar", w["gauge_seed"], nd=3)
+    vecs = synth.gaussian_vectors(dims, 12, w["vec_seed"], dtype=torch.complex64, device="cuda")
+    st = getattr(T, "TLS_" + storage)
+    gid = ctx.load_gauge(U, 3, dims)
+    ctx.build_twolink(gid, getattr(T, "TLS_" + wprec), recon)
+    ref = {(v, t): vecs[v, t:t + 1].cpu().numpy().astype(np.complex128) for v, t in ((0, 0), (7, 41))}
+    ctx.smear(gid, vecs, T.TLS_F32, 12, w["N"], w["sigma"], storage=st, kernel=T.TLS_KERNEL_MRHS)
+    ctx.free_gauge(gid)
+    for (v, t), src in ref.items():
+        want = oracle.smear(oracle.twolink(U[t:t + 1].cpu().numpy()), src, w["N"], w["sigma"])
+        got = vecs[v, t:t + 1].cpu().numpy().astype(np.complex128)
+        assert rel_l2(got, want) <= tol(st, w["N"])
