@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "single", "mrhs", "persistent"])
     ap.add_argument("--small", action="store_true", help="16^3x8 lattice, for quick checks only")
+    ap.add_argument("--lattice", default=None, help="Lx,Ly,Lz,Lt override (profiling cases)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (planner default)")
     ap.add_argument("--no-extra", action="store_true", help="skip e2e, cpu baseline and side measurements")
     return ap.parse_args()
 
@@ -61,6 +63,17 @@ def dist_setup(backend):
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """The largest value of x over all ranks (the job is as slow as its slowest rank)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -70,11 +83,14 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def workload(small):
+def workload(small, lattice=None):
     from paper_2301_05518_gb300 import workloads
     w = dict(workloads.HEADLINE)
     if small:
         w.update(dims=(16, 16, 16, 8), name="16^3x8 24 corner-wall sources N=80 (quick check)")
+    if lattice:
+        dims = tuple(int(x) for x in lattice.split(","))
+        w.update(dims=dims, name="%dx%dx%dx%d 24 corner-wall sources N=80 (profiling case)" % dims)
     return w
 
 
@@ -157,7 +173,7 @@ def reference_arm(args):
     import torch
     import oracle
     from paper_2301_05518_gb300 import synth
-    w = workload(args.small)
+    w = workload(args.small, args.lattice)
     oracle.build()
     Lx, Ly, Lz, Lt = w["dims"]
     nsl = 4
@@ -195,7 +211,7 @@ def our_arm(args):
     torch.cuda.set_device(local)
     from paper_2301_05518_gb300 import tls
     T = tls
-    w = workload(args.small)
+    w = workload(args.small, args.lattice)
     dims = w["dims"]
     Lx, Ly, Lz, Lt = dims
     V = Lx * Ly * Lz * Lt
@@ -214,6 +230,15 @@ def our_arm(args):
 
     launches_per_step = [0]
     prof_last = {}
+    tune = None
+    if kernel == T.TLS_KERNEL_AUTO and not args.no_tune:
+        gid = ctx.load_gauge(U, 4, dims, stream=stream)
+        ctx.build_twolink(gid, wprec, T.TLS_R18, keep_U=0, stream=stream)
+        best, cands = ctx.autotune(gid, nvec, storage, T.TLS_ALL_T, steps=4)
+        ctx.free_gauge(gid)
+        names = {1: "single", 2: "mrhs", 3: "persistent"}
+        tune = {"best": dict(best, kernel=names[best["kernel"]]),
+                "candidates": [dict(c, kernel=names[c["kernel"]]) for c in cands]}
 
     def step(Uin, x):
         gid = ctx.load_gauge(Uin, 4, dims, stream=stream)
@@ -250,10 +275,7 @@ def our_arm(args):
     barrier()
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
-    t_local = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t_local.item())
+    ms_max = max_over_ranks(ms_total, ws, "cuda")
     ms_per_step = ms_max / args.steps
     value = ws * nvec * args.steps / (ms_max / 1e3)
 
@@ -271,7 +293,8 @@ def our_arm(args):
             "note": ("algorithmic bytes = W once + psi read once + psi written once per site and "
                      "step; persistent launches count all N steps (effective GB/s)")}
 
-    extra = {"breakdown_ms": {k: prof_last[k] for k in ("ms_pack", "ms_iter", "ms_unpack")},
+    extra = {"autotune": tune,
+             "breakdown_ms": {k: prof_last[k] for k in ("ms_pack", "ms_iter", "ms_unpack")},
              "build_ms": prof_last["ms_build"], "kernel": kern_name,
              "vecs_per_thread": prof_last["vecs_per_thread"]}
 

@@ -192,6 +192,29 @@ tls_status tls_get_profile(tls_ctx *ctx, tls_profile *out);
  * A tiny budget forces the TLS_ERR_TIMEOUT path without hanging the GPU.   */
 tls_status tls_set_barrier_budget(tls_ctx *ctx, int64_t polls);
 
+/* ---- autotuning ------------------------------------------------------------
+ * Candidate kernels for one problem shape, each timed with CUDA events over
+ * `steps` smearing steps on scratch vectors of the context's device.        */
+typedef struct {
+    int kernel;             /* TLS_KERNEL_SINGLE, _MRHS or _PERSISTENT         */
+    int vecs_per_thread;    /* vectors per thread (planar kernels)             */
+    int threads;            /* threads per CTA                                 */
+    double ms_per_step;     /* measured time of one smearing step              */
+} tls_tune_entry;
+
+/* Times every candidate for smearing nvec vectors of gauge `id` stored in
+ * `storage` on `timeslice` (TLS_ALL_T or a slice), keeps the fastest in the
+ * context's table (used by TLS_KERNEL_AUTO for that shape) and returns it in
+ * *best (nullable).  Up to max_all candidates are written to `all`
+ * (nullable) and their number to *n_all (nullable).  The vectors it smears
+ * are scratch: caller data is not touched.  Errors as tls_smear.           */
+tls_status tls_autotune(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, int timeslice, int steps,
+                        tls_tune_entry *best, tls_tune_entry *all, int max_all, int *n_all);
+
+/* Sets the table entry for a shape by hand (e.g. from a saved autotune).   */
+tls_status tls_tune_set(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, int timeslice,
+                        const tls_tune_entry *entry);
+
 /* ---- serving: continuous batching of smearing jobs (Sec. 6 pattern) ---------
  * A scheduler thread keeps each gauge field's W resident, admits jobs while
  * the context's HBM cap allows, packs the vectors of compatible jobs into the
@@ -234,7 +257,9 @@ tls_status tls_serve_stop(tls_ctx *ctx);
  * fit under the HBM cap.                                                   */
 tls_status tls_serve_submit(tls_ctx *ctx, const tls_job *job, uint64_t *job_id);
 tls_status tls_serve_poll(tls_ctx *ctx, uint64_t job_id, int *done);
-/* Blocks until the job finishes or timeout_s passes (TLS_ERR_TIMEOUT).     */
+/* Blocks until the job finishes or timeout_s passes (TLS_ERR_TIMEOUT), fills
+ * *result (nullable) and releases the job record: a later poll or wait on
+ * the same id returns TLS_ERR_NOT_FOUND.  Returns the job's own status.     */
 tls_status tls_serve_wait(tls_ctx *ctx, uint64_t job_id, double timeout_s,
                           tls_job_result *result);
 

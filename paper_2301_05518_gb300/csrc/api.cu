@@ -125,6 +125,17 @@ cudaError_t launch_step(const StepArgs &a)
     }
 }
 
+cudaError_t launch_step_il(const StepArgs &a)
+{
+    switch (a.prec_in) {
+    case P_F64: return launch_step_il_f64(a);
+    case P_F32: return launch_step_il_f32(a);
+    case P_F16: return launch_step_il_f16(a);
+    case P_BF16: return launch_step_il_bf16(a);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 cudaError_t launch_persistent(const PersistArgs &a)
 {
     switch (a.prec) {
@@ -383,6 +394,8 @@ tls_status tls_free_gauge(tls_ctx *ctx, tls_gauge_id id)
     Gauge *gg = find_gauge(ctx, id);
     if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_free_gauge: unknown gauge id %lld", (long long)id);
     cudaSetDevice(ctx->device);
+    if (serve_gauge_busy(ctx, id))
+        return fail(TLS_ERR_STATE, "tls_free_gauge: serving jobs still use gauge %lld", (long long)id);
     cudaDeviceSynchronize();
     free_gauge(ctx, *gg);
     ctx->gauges.erase(id);
@@ -436,6 +449,18 @@ static float elapsed(cudaEvent_t a, cudaEvent_t b)
 tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec, int N,
                      double width, int timeslice, int storage, int kernel, void *stream, double *norms_out)
 {
+    return smear_impl(ctx, id, vecs, io_prec, vecs_on_device, nvec, N, width, timeslice, storage, kernel, 0, 0,
+                      stream, norms_out);
+}
+
+}  // extern "C"
+
+namespace tls {
+
+tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec, int N,
+                      double width, int timeslice, int storage, int kernel, int force_vb, int force_threads,
+                      void *stream, double *norms_out)
+{
     if (!ctx || !vecs) return fail(TLS_ERR_ARG, "tls_smear: NULL argument");
     if (io_prec != TLS_F64 && io_prec != TLS_F32)
         return fail(TLS_ERR_ARG, "tls_smear: io_prec %d must be TLS_F64 or TLS_F32", io_prec);
@@ -469,7 +494,7 @@ tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int
     // Kernel choice.
     int kern = kernel;
     int vb = default_vb(storage, nvec);
-    int threads = 128;
+    int threads = 0;
     if (kern == TLS_KERNEL_AUTO) {
         TuneKey key{{gg->L[0], gg->L[1], gg->L[2], gg->L[3]}, nsl, nvec, storage, gg->wfmt};
         auto it = ctx->tune.find(key);
@@ -478,22 +503,34 @@ tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int
             vb = it->second.vb;
             threads = it->second.threads;
         } else {
-            kern = nvec == 1 ? TLS_KERNEL_PERSISTENT : TLS_KERNEL_MRHS;
+            kern = nvec == 1 ? TLS_KERNEL_SINGLE : TLS_KERNEL_MRHS;
+        }
+    } else {
+        TuneKey key{{gg->L[0], gg->L[1], gg->L[2], gg->L[3]}, nsl, nvec, storage, gg->wfmt};
+        auto it = ctx->tune.find(key);
+        if (it != ctx->tune.end() && it->second.kernel == kern) {
+            vb = it->second.vb;
+            threads = it->second.threads;
         }
     }
+    if (force_vb > 0) vb = force_vb;
+    if (force_threads > 0) threads = force_threads;
     if (kern == TLS_KERNEL_SINGLE) vb = 1;
     if (kern == TLS_KERNEL_PERSISTENT) {
-        threads = 256;
+        if (threads <= 0) threads = 256;
         if (vb == 2) vb = 1;
     }
+    if (threads <= 0) threads = kern == TLS_KERNEL_MRHS ? 256 : 128;
+    // The multi-RHS kernel works on the interleaved layout in groups of <= 256 vectors.
+    const int G = kern == TLS_KERNEL_MRHS ? std::min(nvec, 256) : nvec;
 
     // Workspace.
-    size_t a_bytes = (size_t)vs * nvec;
+    size_t a_bytes = (size_t)vs * G;
     s = ensure(ctx, ctx->A, a_bytes, "tls_smear: vector buffer A");
     if (s == TLS_OK) s = ensure(ctx, ctx->B, a_bytes, "tls_smear: vector buffer B");
     if (s == TLS_OK) s = ensure(ctx, ctx->alpha, sizeof(double) * nvec, "tls_smear: alpha");
-    const int nparts = unpack_parts(g, nsl);
-    if (s == TLS_OK && norms_out) s = ensure(ctx, ctx->partials, sizeof(double) * nparts * nvec, "tls_smear: partials");
+    if (s == TLS_OK && norms_out)
+        s = ensure(ctx, ctx->partials, sizeof(double) * kNormParts * nvec, "tls_smear: partials");
     if (s == TLS_OK && norms_out) s = ensure(ctx, ctx->norms, sizeof(double) * nvec, "tls_smear: norms");
     if (s == TLS_OK && !vecs_on_device)
         s = ensure(ctx, ctx->staging, io_slice_bytes * nsl * nvec, "tls_smear: host staging");
@@ -543,7 +580,20 @@ tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int
     cudaError_t e = cudaSuccess;
     int64_t launches = 0, iter_launches = 0;
     const bool prof = ctx->profiling;
-    if (prof) cudaEventRecord(ctx->ev[0], st);
+    float t_pack = 0, t_iter = 0, t_unpack = 0, t_h2d = 0, t_d2h = 0;
+    // Phase timing: events on the launch stream, accumulated per vector group.
+    auto mark = [&](int k) {
+        if (prof) cudaEventRecord(ctx->ev[k], st);
+    };
+    auto lap = [&](int a0, int a1) -> float {
+        float ms = 0.f;
+        if (prof) {
+            cudaEventSynchronize(ctx->ev[a1]);
+            cudaEventElapsedTime(&ms, ctx->ev[a0], ctx->ev[a1]);
+        }
+        return ms;
+    };
+    mark(0);
     e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->alpha.p, ctx->h_alpha, sizeof(double) * nvec, cudaMemcpyHostToDevice, st);
@@ -567,90 +617,112 @@ tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int
         io_vstride_sites = Vslice * nsl;
         t_rel = 0;
     }
-    if (prof) cudaEventRecord(ctx->ev[1], st);
-    if (e == cudaSuccess) {
-        e = launch_pack_vectors(src_io, io_prec, io_vstride_sites, (char *)ctx->A.p, storage, vs, g, gg->L, t_rel,
-                                nsl, nvec, st);
-        ++launches;
-    }
-    if (prof) cudaEventRecord(ctx->ev[2], st);
+    mark(1);
+    if (prof) t_h2d = lap(0, 1);
 
     const char *W0 = gg->W + (size_t)t_first * 8 * 3 * g.Ps * wfmt_bytes(gg->wfmt);
-    char *result = (char *)ctx->A.p;
-    if (N > 0 && e == cudaSuccess) {
-        if (kern == TLS_KERNEL_PERSISTENT) {
-            pa.W = W0;
-            pa.in = (const char *)ctx->A.p;
-            pa.out = (char *)ctx->B.p;
-            pa.scr[0] = (char *)ctx->S0.p;
-            pa.scr[1] = (char *)ctx->S1.p;
-            pa.alpha = (const double *)ctx->alpha.p;
-            pa.g = g;
-            pa.nblk = nblk;
-            pa.nvec = nvec;
-            pa.N = N;
-            pa.vstride = vs;
-            pa.wfmt = gg->wfmt;
-            pa.prec = storage;
-            pa.vb = vb;
-            pa.threads = threads;
-            pa.bar = ctx->d_bar;
-            pa.err = ctx->d_err;
-            pa.budget = ctx->barrier_budget > 0 ? ctx->barrier_budget : kDefaultBudget;
-            pa.stream = st;
-            e = cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), st);
-            if (e == cudaSuccess) e = launch_persistent(pa);
-            ++launches;
-            ++iter_launches;
-            result = (char *)ctx->B.p;
-        } else {
-            StepArgs sa{};
-            sa.W = W0;
-            sa.g = g;
-            sa.nblk = nblk;
-            sa.wfmt = gg->wfmt;
-            sa.prec_in = sa.prec_out = storage;
-            sa.vb = vb;
-            sa.threads = threads;
-            sa.stream = st;
-            sa.vstride_in = sa.vstride_out = vs;
-            const int groups = kern == TLS_KERNEL_SINGLE ? nvec : 1;
-            sa.nvec = kern == TLS_KERNEL_SINGLE ? 1 : nvec;
-            for (int gi = 0; gi < groups && e == cudaSuccess; ++gi) {
-                char *x = (char *)ctx->A.p + (size_t)gi * vs;
-                char *y = (char *)ctx->B.p + (size_t)gi * vs;
-                for (int it = 0; it < N && e == cudaSuccess; ++it) {
-                    sa.in = (it & 1) ? y : x;
-                    sa.out = (it & 1) ? x : y;
-                    sa.alpha = (const double *)ctx->alpha.p + gi;
-                    e = launch_step(sa);
-                    ++launches;
-                    ++iter_launches;
+    const size_t io_vec_bytes = (size_t)io_vstride_sites * 6 * io_elem;
+    for (int g0 = 0; g0 < nvec && e == cudaSuccess; g0 += G) {
+        const int gn = std::min(G, nvec - g0);
+        const char *src_g = src_io + (size_t)g0 * io_vec_bytes;
+        char *dst_g = dst_io + (size_t)g0 * io_vec_bytes;
+        const bool il = kern == TLS_KERNEL_MRHS;
+        mark(2);
+        e = il ? launch_pack_il(src_g, io_prec, io_vstride_sites, (char *)ctx->A.p, storage, g, gg->L, t_rel, nsl, gn,
+                                    gn, 0, st)
+               : launch_pack_vectors(src_g, io_prec, io_vstride_sites, (char *)ctx->A.p, storage, vs, g, gg->L, t_rel,
+                                     nsl, gn, st);
+        ++launches;
+        mark(3);
+        char *result = (char *)ctx->A.p;
+        const double *alpha_g = (const double *)ctx->alpha.p + g0;
+        if (N > 0 && e == cudaSuccess) {
+            if (kern == TLS_KERNEL_PERSISTENT) {
+                pa.W = W0;
+                pa.in = (const char *)ctx->A.p;
+                pa.out = (char *)ctx->B.p;
+                pa.scr[0] = (char *)ctx->S0.p;
+                pa.scr[1] = (char *)ctx->S1.p;
+                pa.alpha = alpha_g;
+                pa.g = g;
+                pa.nblk = nblk;
+                pa.nvec = gn;
+                pa.N = N;
+                pa.vstride = vs;
+                pa.wfmt = gg->wfmt;
+                pa.prec = storage;
+                pa.vb = vb;
+                pa.threads = threads;
+                pa.bar = ctx->d_bar;
+                pa.err = ctx->d_err;
+                pa.budget = ctx->barrier_budget > 0 ? ctx->barrier_budget : kDefaultBudget;
+                pa.stream = st;
+                e = cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), st);
+                if (e == cudaSuccess) e = launch_persistent(pa);
+                ++launches;
+                ++iter_launches;
+                result = (char *)ctx->B.p;
+            } else {
+                StepArgs sa{};
+                sa.W = W0;
+                sa.g = g;
+                sa.nblk = nblk;
+                sa.wfmt = gg->wfmt;
+                sa.prec_in = sa.prec_out = storage;
+                sa.vb = vb;
+                sa.threads = threads;
+                sa.stream = st;
+                sa.vstride_in = sa.vstride_out = vs;
+                const int sub_groups = kern == TLS_KERNEL_SINGLE ? gn : 1;
+                sa.nvec = kern == TLS_KERNEL_SINGLE ? 1 : gn;
+                for (int gi = 0; gi < sub_groups && e == cudaSuccess; ++gi) {
+                    char *x = (char *)ctx->A.p + (size_t)gi * vs;
+                    char *y = (char *)ctx->B.p + (size_t)gi * vs;
+                    for (int it = 0; it < N && e == cudaSuccess; ++it) {
+                        sa.in = (it & 1) ? y : x;
+                        sa.out = (it & 1) ? x : y;
+                        sa.alpha = alpha_g + gi;
+                        e = il ? launch_step_il(sa) : launch_step(sa);
+                        ++launches;
+                        ++iter_launches;
+                    }
                 }
+                result = (N & 1) ? (char *)ctx->B.p : (char *)ctx->A.p;
             }
-            result = (N & 1) ? (char *)ctx->B.p : (char *)ctx->A.p;
+        }
+        mark(4);
+        if (e == cudaSuccess) {
+            e = il ? launch_unpack_il(result, storage, dst_g, io_prec, io_vstride_sites, g, gg->L, t_rel, nsl, gn, gn, 0,
+                                      st)
+                   : launch_unpack_vectors(result, storage, vs, dst_g, io_prec, io_vstride_sites, g, gg->L, t_rel, nsl,
+                                           gn, nullptr, nullptr, st);
+            ++launches;
+        }
+        mark(5);
+        if (prof) {
+            t_pack += lap(2, 3);
+            t_iter += lap(3, 4);
+            t_unpack += lap(4, 5);
         }
     }
-    if (prof) cudaEventRecord(ctx->ev[3], st);
-    if (e == cudaSuccess) {
-        e = launch_unpack_vectors(result, storage, vs, dst_io, io_prec, io_vstride_sites, g, gg->L, t_rel, nsl, nvec,
-                                  norms_out ? (double *)ctx->partials.p : nullptr, nullptr, st);
-        ++launches;
-    }
     if (e == cudaSuccess && norms_out) {
-        e = launch_reduce_norms((const double *)ctx->partials.p, nparts, nvec, (double *)ctx->norms.p, st);
-        ++launches;
+        // ||psi_v||^2 over the smeared slices of the canonical result.
+        const char *first = dst_io + (size_t)t_rel * io_slice_bytes;
+        e = launch_norm_partials(first, io_prec, io_vstride_sites, Vslice * nsl, nvec, (double *)ctx->partials.p, st);
+        if (e == cudaSuccess)
+            e = launch_reduce_norms((const double *)ctx->partials.p, kNormParts, nvec, (double *)ctx->norms.p, st);
+        launches += 2;
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ctx->h_norms, ctx->norms.p, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st);
     }
-    if (prof) cudaEventRecord(ctx->ev[4], st);
+    mark(6);
     if (e == cudaSuccess && !vecs_on_device) {
         const size_t width_b = io_slice_bytes * nsl;
         const size_t pitch = (size_t)V * 6 * io_elem;
         e = cudaMemcpy2DAsync((char *)vecs + (size_t)t_first * io_slice_bytes, pitch, ctx->staging.p, width_b,
                               width_b, nvec, cudaMemcpyDeviceToHost, st);
     }
-    if (prof) cudaEventRecord(ctx->ev[5], st);
+    mark(7);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t es = cudaStreamSynchronize(st);
@@ -660,21 +732,21 @@ tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int
     if (prof) {
         tls_profile &p = ctx->prof;
         p = tls_profile{};
-        p.ms_total = elapsed(ctx->ev[0], ctx->ev[5]);
-        p.ms_h2d = elapsed(ctx->ev[0], ctx->ev[1]);
-        p.ms_pack = elapsed(ctx->ev[1], ctx->ev[2]);
-        p.ms_iter = elapsed(ctx->ev[2], ctx->ev[3]);
-        p.ms_unpack = elapsed(ctx->ev[3], ctx->ev[4]);
-        p.ms_d2h = elapsed(ctx->ev[4], ctx->ev[5]);
+        p.ms_total = elapsed(ctx->ev[0], ctx->ev[7]);
+        p.ms_h2d = t_h2d;
+        p.ms_pack = t_pack;
+        p.ms_iter = t_iter;
+        p.ms_unpack = t_unpack + elapsed(ctx->ev[5], ctx->ev[6]);
+        p.ms_d2h = elapsed(ctx->ev[6], ctx->ev[7]);
         p.launches = launches;
         p.iter_launches = iter_launches;
         const double sites = (double)nblk * g.Vs;
         const double wb = 3.0 * wfmt_bytes(gg->wfmt), vbb = 2.0 * VBY;
         p.iter_bytes = kern == TLS_KERNEL_SINGLE ? (double)N * nvec * sites * (wb + vbb)
-                                                 : (double)N * sites * (wb + nvec * vbb);
+                                                 : (double)N * sites * (wb * ((nvec + G - 1) / G) + nvec * vbb);
         p.iter_flops = 450.0 * N * nvec * sites;
         p.kernel = kern;
-        p.vecs_per_thread = vb;
+        p.vecs_per_thread = kern == TLS_KERNEL_MRHS ? 1 : vb;
     }
     if (herr & DERR_TIMEOUT)
         return fail(TLS_ERR_TIMEOUT, "tls_smear: a bounded inter-block barrier of the persistent kernel ran out");
@@ -683,4 +755,4 @@ tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int
     return ok();
 }
 
-}  // extern "C"
+}  // namespace tls

@@ -100,7 +100,14 @@ void release(tls_ctx *ctx, DevBuf &b);
 tls_status check_smear_combo(const Gauge &gg, int storage);
 int default_vb(int storage, int nvec);
 
+// tls_smear with an optional forced vectors-per-thread / threads (0 = planner's choice).
+tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec, int N,
+                      double width, int timeslice, int storage, int kernel, int force_vb, int force_threads,
+                      void *stream, double *norms_out);
+
 // The serving subsystem (serve.cpp).
 void serve_shutdown(tls_ctx *ctx);
+// True if serving still holds jobs on gauge `id`; otherwise drops its idle batches.
+bool serve_gauge_busy(tls_ctx *ctx, int64_t id);
 
 }  // namespace tls

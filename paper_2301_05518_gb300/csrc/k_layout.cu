@@ -10,6 +10,8 @@
 //
 // Packed U layout: block b = t * 8 + sub, direction d, entry k = 0..8:
 //   Up[((b * 3 + d) * 9 + k) * Ps + i]  (double2 = one complex entry)
+#include <algorithm>
+
 #include "tls_dev.cuh"
 #include "tls_internal.h"
 
@@ -227,6 +229,79 @@ __global__ void __launch_bounds__(256) k_reduce_norms(const double *__restrict__
     if (threadIdx.x == 0) norms[v] = red[0];
 }
 
+// Interleaved layout: CTA = (nvec, spb); threadIdx.x = vector, threadIdx.y = site.
+template <typename IO, int VP>
+__global__ void k_pack_il(const IO *__restrict__ src, int64_t svs, char *__restrict__ dst, SubGeom g, int Lx, int Ly,
+                          int Lz, int t_first, int64_t nsite, int rec_n, int rec_v0)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    if (s >= nsite) return;
+    const int v = threadIdx.x;
+    const int b = (int)(s / g.Vs);
+    const int i = (int)(s - (int64_t)b * g.Vs);
+    const int t = t_first + (b >> 3), sub = b & 7;
+    Coords c = coords_of(g, sub, i);
+    const int64_t site = (((int64_t)t * Lz + c.z) * Ly + c.y) * Lx + c.x;
+    const IO *p = src + ((int64_t)v * svs + site) * 6;
+    typedef typename VRec<VP>::R R;
+    cpx<R> val[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        val[k].re = (R)p[2 * k];
+        val[k].im = (R)p[2 * k + 1];
+    }
+    VRec<VP>::store(dst + (((int64_t)b * g.Ps + i) * rec_n + rec_v0 + v) * vfmt_bytes(VP), val);
+}
+
+template <typename IO, int VP>
+__global__ void k_unpack_il(const char *__restrict__ src, IO *__restrict__ dst, int64_t dvs, SubGeom g, int Lx,
+                            int Ly, int Lz, int t_first, int64_t nsite, int rec_n, int rec_v0)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    if (s >= nsite) return;
+    const int v = threadIdx.x;
+    const int b = (int)(s / g.Vs);
+    const int i = (int)(s - (int64_t)b * g.Vs);
+    const int t = t_first + (b >> 3), sub = b & 7;
+    Coords c = coords_of(g, sub, i);
+    const int64_t site = (((int64_t)t * Lz + c.z) * Ly + c.y) * Lx + c.x;
+    typedef typename VRec<VP>::R R;
+    cpx<R> val[3];
+    VRec<VP>::load(src + (((int64_t)b * g.Ps + i) * rec_n + rec_v0 + v) * vfmt_bytes(VP), val);
+    IO *p = dst + ((int64_t)v * dvs + site) * 6;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[2 * k] = (IO)val[k].re;
+        p[2 * k + 1] = (IO)val[k].im;
+    }
+}
+
+// Partial sums of |psi|^2 over `count` sites of each canonical vector:
+// CTA (part, v) takes a fixed strided subset, so the sum order is fixed.
+template <typename IO>
+__global__ void __launch_bounds__(256) k_norm_partials(const IO *__restrict__ base, int64_t vstride, int64_t count,
+                                                       double *__restrict__ partials)
+{
+    __shared__ double red[256];
+    const int v = blockIdx.y;
+    const IO *p = base + (int64_t)v * vstride * 6;
+    const int64_t n = count * 6;
+    double acc = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double x = (double)p[k];
+        acc = fma(x, x, acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[(int64_t)v * gridDim.x + blockIdx.x] = red[0];
+}
+
+inline int spb_of(int nvec) { return std::max(1, 256 / nvec); }
+
 inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <typename IO>
@@ -351,6 +426,84 @@ cudaError_t launch_unpack_vectors(const char *src, int prec, int64_t src_vstride
         return unpack_io<float>(src, prec, src_vstride, (float *)dst, dst_vstride_sites, g, L, t_first, nsite, nvec,
                                 partials, s);
     return cudaErrorNotSupported;
+}
+
+template <typename IO>
+static cudaError_t pack_il_io(const IO *src, int64_t svs, char *dst, int prec, const SubGeom &g, const int L[4],
+                              int t_first, int64_t nsite, int nvec, int rec_n, int rec_v0, cudaStream_t s)
+{
+    const int spb = spb_of(nvec);
+    dim3 block(nvec, spb), grid(nblocks(nsite, spb));
+    switch (prec) {
+    case P_F64: k_pack_il<IO, P_F64><<<grid, block, 0, s>>>(src, svs, dst, g, L[0], L[1], L[2], t_first, nsite, rec_n, rec_v0); break;
+    case P_F32: k_pack_il<IO, P_F32><<<grid, block, 0, s>>>(src, svs, dst, g, L[0], L[1], L[2], t_first, nsite, rec_n, rec_v0); break;
+    case P_F16: k_pack_il<IO, P_F16><<<grid, block, 0, s>>>(src, svs, dst, g, L[0], L[1], L[2], t_first, nsite, rec_n, rec_v0); break;
+    case P_BF16: k_pack_il<IO, P_BF16><<<grid, block, 0, s>>>(src, svs, dst, g, L[0], L[1], L[2], t_first, nsite, rec_n, rec_v0); break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+template <typename IO>
+static cudaError_t unpack_il_io(const char *src, int prec, IO *dst, int64_t dvs, const SubGeom &g, const int L[4],
+                                int t_first, int64_t nsite, int nvec, int rec_n, int rec_v0, cudaStream_t s)
+{
+    const int spb = spb_of(nvec);
+    dim3 block(nvec, spb), grid(nblocks(nsite, spb));
+    switch (prec) {
+    case P_F64: k_unpack_il<IO, P_F64><<<grid, block, 0, s>>>(src, dst, dvs, g, L[0], L[1], L[2], t_first, nsite, rec_n, rec_v0); break;
+    case P_F32: k_unpack_il<IO, P_F32><<<grid, block, 0, s>>>(src, dst, dvs, g, L[0], L[1], L[2], t_first, nsite, rec_n, rec_v0); break;
+    case P_F16: k_unpack_il<IO, P_F16><<<grid, block, 0, s>>>(src, dst, dvs, g, L[0], L[1], L[2], t_first, nsite, rec_n, rec_v0); break;
+    case P_BF16: k_unpack_il<IO, P_BF16><<<grid, block, 0, s>>>(src, dst, dvs, g, L[0], L[1], L[2], t_first, nsite, rec_n, rec_v0); break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_il(const void *src, int io_prec, int64_t src_vstride_sites, char *dst, int prec,
+                           const SubGeom &g, const int L[4], int t_first, int nsl, int nvec, int rec_n, int rec_v0,
+                           cudaStream_t s)
+{
+    const int64_t nsite = (int64_t)nsl * 8 * g.Vs;
+    if (nsite == 0 || nvec == 0) return cudaSuccess;
+    if (nvec > 256 || rec_v0 < 0 || rec_v0 + nvec > rec_n) return cudaErrorInvalidValue;
+    if (io_prec == P_F64)
+        return pack_il_io<double>((const double *)src, src_vstride_sites, dst, prec, g, L, t_first, nsite, nvec, rec_n,
+                                  rec_v0, s);
+    if (io_prec == P_F32)
+        return pack_il_io<float>((const float *)src, src_vstride_sites, dst, prec, g, L, t_first, nsite, nvec, rec_n,
+                                 rec_v0, s);
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_unpack_il(const char *src, int prec, void *dst, int io_prec, int64_t dst_vstride_sites,
+                             const SubGeom &g, const int L[4], int t_first, int nsl, int nvec, int rec_n, int rec_v0,
+                             cudaStream_t s)
+{
+    const int64_t nsite = (int64_t)nsl * 8 * g.Vs;
+    if (nsite == 0 || nvec == 0) return cudaSuccess;
+    if (nvec > 256 || rec_v0 < 0 || rec_v0 + nvec > rec_n) return cudaErrorInvalidValue;
+    if (io_prec == P_F64)
+        return unpack_il_io<double>(src, prec, (double *)dst, dst_vstride_sites, g, L, t_first, nsite, nvec, rec_n,
+                                    rec_v0, s);
+    if (io_prec == P_F32)
+        return unpack_il_io<float>(src, prec, (float *)dst, dst_vstride_sites, g, L, t_first, nsite, nvec, rec_n,
+                                   rec_v0, s);
+    return cudaErrorNotSupported;
+}
+
+cudaError_t launch_norm_partials(const void *base, int io_prec, int64_t vstride_sites, int64_t count, int nvec,
+                                 double *partials, cudaStream_t s)
+{
+    if (nvec == 0) return cudaSuccess;
+    dim3 grid(kNormParts, nvec);
+    if (io_prec == P_F64)
+        k_norm_partials<double><<<grid, 256, 0, s>>>((const double *)base, vstride_sites, count, partials);
+    else if (io_prec == P_F32)
+        k_norm_partials<float><<<grid, 256, 0, s>>>((const float *)base, vstride_sites, count, partials);
+    else
+        return cudaErrorNotSupported;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_norms(const double *partials, int nparts, int nvec, double *norms, cudaStream_t s)

@@ -17,6 +17,8 @@
 // (k_step_<prec>.cu) with TLS_VP defined.
 #pragma once
 
+#include <algorithm>
+
 #include "tls_dev.cuh"
 #include "tls_internal.h"
 
@@ -41,7 +43,8 @@ template <int VPI, int VPO, int WF, int VB, bool CGI, bool CGO>
 __device__ __forceinline__ void site_step(const char *__restrict__ W, const char *__restrict__ in,
                                           char *__restrict__ out, const double *__restrict__ alpha,
                                           const SubGeom &g, int wblk, int i, int v0, int nvec, int64_t vs_in,
-                                          int64_t vs_out, int64_t bin, int64_t bout)
+                                          int64_t vs_out, int64_t bin, int64_t bout,
+                                          const int *__restrict__ active = nullptr)
 {
     typedef typename VFmt<VPI>::R R;
     constexpr int WB = wfmt_bytes(WF);
@@ -49,6 +52,14 @@ __device__ __forceinline__ void site_step(const char *__restrict__ W, const char
     sub_neighbours(g, i, fw, bw);
     const char *wb = W + (int64_t)wblk * 3 * g.Ps * WB;
     const char *ib = in + bin;
+    bool on[VB];
+    bool any = false;
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+        on[v] = v0 + v < nvec && (active == nullptr || active[v0 + v] != 0);
+        any = any || on[v];
+    }
+    if (!any) return;
     cpx<R> acc[VB][3];
 #pragma unroll
     for (int v = 0; v < VB; ++v)
@@ -61,7 +72,7 @@ __device__ __forceinline__ void site_step(const char *__restrict__ W, const char
         WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, i, m);
 #pragma unroll
         for (int v = 0; v < VB; ++v) {
-            if (v0 + v < nvec) {
+            if (on[v]) {
                 cpx<R> p[3];
                 VFmt<VPI>::template load<CGI>(ib + (int64_t)(v0 + v) * vs_in, g.Ps, fw[d], p);
                 mv_add(m, p, acc[v]);
@@ -70,7 +81,7 @@ __device__ __forceinline__ void site_step(const char *__restrict__ W, const char
         WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, bw[d], m);
 #pragma unroll
         for (int v = 0; v < VB; ++v) {
-            if (v0 + v < nvec) {
+            if (on[v]) {
                 cpx<R> p[3];
                 VFmt<VPI>::template load<CGI>(ib + (int64_t)(v0 + v) * vs_in, g.Ps, bw[d], p);
                 mdv_add(m, p, acc[v]);
@@ -79,7 +90,7 @@ __device__ __forceinline__ void site_step(const char *__restrict__ W, const char
     }
 #pragma unroll
     for (int v = 0; v < VB; ++v) {
-        if (v0 + v < nvec) {
+        if (on[v]) {
             cpx<R> c[3], o[3];
             VFmt<VPI>::template load<CGI>(ib + (int64_t)(v0 + v) * vs_in, g.Ps, i, c);
             const R a = (R)alpha[v0 + v];
@@ -106,7 +117,8 @@ __device__ __forceinline__ void item_of(int64_t w, int nchunk, int64_t &site, in
 template <int VP, int WF, int VB>
 __global__ void __launch_bounds__(256) k_step(const char *__restrict__ W, const char *__restrict__ in,
                                               char *__restrict__ out, const double *__restrict__ alpha,
-                                              SubGeom g, int nblk, int nvec, int64_t vs_in, int64_t vs_out)
+                                              const int *__restrict__ active, SubGeom g, int nblk, int nvec,
+                                              int64_t vs_in, int64_t vs_out)
 {
     const int nchunk = (nvec + VB - 1) / VB;
     int64_t site;
@@ -118,7 +130,68 @@ __global__ void __launch_bounds__(256) k_step(const char *__restrict__ W, const 
     constexpr int VBY = vfmt_bytes(VP);
     const int64_t boff = (int64_t)blk * g.Ps * VBY;
     site_step<VP, VP, WF, VB, false, false>(W, in, out, alpha, g, blk, i, chunk * VB, nvec, vs_in, vs_out, boff,
-                                            boff);
+                                            boff, active);
+}
+
+// --------------------------------------------------------------------------
+// Multi-RHS step on the interleaved layout (vectors innermost).
+// CTA = (nvec, spb) threads: threadIdx.x is the vector, threadIdx.y one of
+// spb consecutive sites along x' of the row (y' = blockIdx.y, z' and the
+// block from blockIdx.z).  All lanes of a site read the same W words (one
+// broadcast), and the records of consecutive (site, vector) pairs are
+// contiguous, so every vector load and store is coalesced.  No index
+// division: the neighbours come from the grid coordinates.  The arithmetic
+// per vector is the same sequence as site_step, so results are bitwise equal
+// to the planar kernels.
+// --------------------------------------------------------------------------
+template <int VP, int WF>
+__global__ void __launch_bounds__(256) k_step_il(const char *__restrict__ W, const char *__restrict__ in,
+                                                 char *__restrict__ out, const double *__restrict__ alpha,
+                                                 const int *__restrict__ active, SubGeom g, int nvec)
+{
+    typedef typename VRec<VP>::R R;
+    constexpr int WB = wfmt_bytes(WF);
+    constexpr int VBY = vfmt_bytes(VP);
+    const int v = threadIdx.x;
+    const int xq = blockIdx.x * blockDim.y + threadIdx.y;
+    if (xq >= g.hx) return;
+    if (active != nullptr && active[v] == 0) return;
+    const int yq = blockIdx.y;
+    const int blk = blockIdx.z / g.hz;
+    const int zq = blockIdx.z - blk * g.hz;
+    const int sy = g.hx, sz = g.hx * g.hy;
+    const int i = zq * sz + yq * sy + xq;
+    int fw[3], bw[3];
+    fw[0] = xq == g.hx - 1 ? i - (g.hx - 1) : i + 1;
+    bw[0] = xq == 0 ? i + (g.hx - 1) : i - 1;
+    fw[1] = yq == g.hy - 1 ? i - (g.hy - 1) * sy : i + sy;
+    bw[1] = yq == 0 ? i + (g.hy - 1) * sy : i - sy;
+    fw[2] = zq == g.hz - 1 ? i - (g.hz - 1) * sz : i + sz;
+    bw[2] = zq == 0 ? i + (g.hz - 1) * sz : i - sz;
+    const char *wb = W + (int64_t)blk * 3 * g.Ps * WB;
+    const int64_t base = (int64_t)blk * g.Ps;
+    cpx<R> acc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c].re = acc[c].im = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        cpx<R> m[9], p[3];
+        WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, i, m);
+        VRec<VP>::load(in + ((base + fw[d]) * nvec + v) * VBY, p);
+        mv_add(m, p, acc);
+        WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, bw[d], m);
+        VRec<VP>::load(in + ((base + bw[d]) * nvec + v) * VBY, p);
+        mdv_add(m, p, acc);
+    }
+    cpx<R> c[3], o[3];
+    VRec<VP>::load(in + ((base + i) * nvec + v) * VBY, c);
+    const R a = (R)alpha[v];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        o[k].re = fma(a, fma(R(-6), c[k].re, acc[k].re), c[k].re);
+        o[k].im = fma(a, fma(R(-6), c[k].im, acc[k].im), c[k].im);
+    }
+    VRec<VP>::store(out + ((base + i) * nvec + v) * VBY, o);
 }
 
 // --------------------------------------------------------------------------
@@ -245,8 +318,8 @@ template <int VP, int WF, int VB> cudaError_t step_launch(const StepArgs &a)
     const int64_t blocks = (items + threads - 1) / threads;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    k_step<VP, WF, VB><<<(unsigned)blocks, threads, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g, a.nblk, a.nvec,
-                                                                   a.vstride_in, a.vstride_out);
+    k_step<VP, WF, VB><<<(unsigned)blocks, threads, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g,
+                                                                   a.nblk, a.nvec, a.vstride_in, a.vstride_out);
     return cudaGetLastError();
 }
 
@@ -265,6 +338,36 @@ template <int VP, int WF, int VB> int persist_occ(int threads)
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<VP, WF, VB>, threads, 0) != cudaSuccess) return 0;
     return n;
+}
+
+// Sites per CTA for the interleaved kernels: nvec * spb <= threads, with a
+// whole number of warps when possible.
+inline int il_spb(int nvec, int threads)
+{
+    if (threads <= 0) threads = 256;
+    int spb = std::max(1, threads / nvec);
+    for (int s = spb; s >= 1; --s)
+        if ((s * nvec) % 32 == 0) return s;
+    return spb;
+}
+
+template <int VP, int WF> cudaError_t step_il_launch(const StepArgs &a)
+{
+    if (a.nvec < 1 || a.nvec > 256) return cudaErrorInvalidValue;
+    const int spb = il_spb(a.nvec, a.threads);
+    dim3 block(a.nvec, spb);
+    dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    k_step_il<VP, WF><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g, a.nvec);
+    return cudaGetLastError();
+}
+
+template <int VP, int WF> cudaError_t step_il_w(const StepArgs &a)
+{
+    if constexpr (!combo_ok<VP, WF>())
+        return cudaErrorNotSupported;
+    else
+        return step_il_launch<VP, WF>(a);
 }
 
 template <int VP, int WF> cudaError_t step_w(const StepArgs &a)
@@ -333,6 +436,12 @@ template <int VP> cudaError_t step_dispatch(const StepArgs &a)
 {
     const int wf = a.wfmt;
     TLS_WFMT_SWITCH(step_w, VP, (a), cudaErrorNotSupported)
+}
+
+template <int VP> cudaError_t step_il_dispatch(const StepArgs &a)
+{
+    const int wf = a.wfmt;
+    TLS_WFMT_SWITCH(step_il_w, VP, (a), cudaErrorNotSupported)
 }
 
 template <int VP> cudaError_t persist_dispatch(const PersistArgs &a)

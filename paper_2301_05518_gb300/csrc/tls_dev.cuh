@@ -392,6 +392,69 @@ template <typename H> struct VFmtH {
 template <> struct VFmt<P_F16> : VFmtH<__half> {};
 template <> struct VFmt<P_BF16> : VFmtH<__nv_bfloat16> {};
 
+// --------------------------------------------------------------------------
+// Interleaved (vector-innermost) records: the nvec vectors of one site are
+// adjacent, record (block, i, v) at ((block * Ps + i) * nvec + v) * bytes.
+// A warp then covers consecutive (site, vector) pairs: vector loads are
+// contiguous and the W of a site is one broadcast for all its lanes.
+//   F64 : 3 x double2 (48 B)   F32 : 3 x float2 (24 B)   16-bit: 16 B record
+// --------------------------------------------------------------------------
+template <int P> struct VRec;
+
+template <> struct VRec<P_F64> {
+    typedef double R;
+    static __device__ __forceinline__ void load(const char *rec, cpx<double> v[3])
+    {
+        const double2 *p = reinterpret_cast<const double2 *>(rec);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double2 a = p[c];
+            v[c].re = a.x;
+            v[c].im = a.y;
+        }
+    }
+    static __device__ __forceinline__ void store(char *rec, const cpx<double> v[3])
+    {
+        double2 *p = reinterpret_cast<double2 *>(rec);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[c] = make_double2(v[c].re, v[c].im);
+    }
+};
+
+template <> struct VRec<P_F32> {
+    typedef float R;
+    static __device__ __forceinline__ void load(const char *rec, cpx<float> v[3])
+    {
+        const float2 *p = reinterpret_cast<const float2 *>(rec);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float2 a = p[c];
+            v[c].re = a.x;
+            v[c].im = a.y;
+        }
+    }
+    static __device__ __forceinline__ void store(char *rec, const cpx<float> v[3])
+    {
+        float2 *p = reinterpret_cast<float2 *>(rec);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[c] = make_float2(v[c].re, v[c].im);
+    }
+};
+
+template <typename H> struct VRecH {
+    typedef float R;
+    static __device__ __forceinline__ void load(const char *rec, cpx<float> v[3])
+    {
+        VFmtH<H>::template load<false>(rec, 0, 0, v);
+    }
+    static __device__ __forceinline__ void store(char *rec, const cpx<float> v[3])
+    {
+        VFmtH<H>::template store<false>(rec, 0, 0, v);
+    }
+};
+template <> struct VRec<P_F16> : VRecH<__half> {};
+template <> struct VRec<P_BF16> : VRecH<__nv_bfloat16> {};
+
 // The six +-1 sublattice neighbours of site i (periodic in h).
 __device__ __forceinline__ void sub_neighbours(const SubGeom &g, int i, int fw[3], int bw[3])
 {

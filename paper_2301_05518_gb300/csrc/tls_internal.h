@@ -14,6 +14,7 @@ struct StepArgs {
     const char *in;        // packed vectors: vector v at in + v * vstride_in
     char *out;
     const double *alpha;   // device, per vector: width / (4 N)
+    const int *active;     // device, per vector (nullable): 0 = leave this vector alone
     SubGeom g;
     int nblk;
     int nvec;
@@ -49,6 +50,8 @@ struct PersistArgs {
 
 // Returns cudaErrorNotSupported for combinations without a kernel.
 cudaError_t launch_step(const StepArgs &a);
+// Interleaved-layout multi-RHS step (nvec <= 256 vectors per record group).
+cudaError_t launch_step_il(const StepArgs &a);
 cudaError_t launch_persistent(const PersistArgs &a);
 // Co-resident CTAs per SM of the persistent kernel for this combination (0: none).
 int persistent_occupancy(int wfmt, int prec, int sprec, int vb, int threads);
@@ -58,6 +61,10 @@ cudaError_t launch_step_f64(const StepArgs &a);
 cudaError_t launch_step_f32(const StepArgs &a);
 cudaError_t launch_step_f16(const StepArgs &a);
 cudaError_t launch_step_bf16(const StepArgs &a);
+cudaError_t launch_step_il_f64(const StepArgs &a);
+cudaError_t launch_step_il_f32(const StepArgs &a);
+cudaError_t launch_step_il_f16(const StepArgs &a);
+cudaError_t launch_step_il_bf16(const StepArgs &a);
 cudaError_t launch_persistent_f64(const PersistArgs &a);
 cudaError_t launch_persistent_f32(const PersistArgs &a);
 cudaError_t launch_persistent_f16(const PersistArgs &a);
@@ -75,6 +82,19 @@ cudaError_t launch_build_twolink(const double *Up, char *W, int wfmt, const SubG
                                  cudaStream_t s);
 cudaError_t launch_export_twolink(const char *W, int wfmt, double *out, const SubGeom &g, const int L[4],
                                   cudaStream_t s);
+// Interleaved layout: rec_n <= 256 records per site, record (block, i, r).  Caller vector v
+// (0 <= v < nvec) goes to / comes from record rec_v0 + v.
+cudaError_t launch_pack_il(const void *src, int io_prec, int64_t src_vstride_sites, char *dst, int prec,
+                           const SubGeom &g, const int L[4], int t_first, int nsl, int nvec, int rec_n, int rec_v0,
+                           cudaStream_t s);
+cudaError_t launch_unpack_il(const char *src, int prec, void *dst, int io_prec, int64_t dst_vstride_sites,
+                             const SubGeom &g, const int L[4], int t_first, int nsl, int nvec, int rec_n, int rec_v0,
+                             cudaStream_t s);
+// FP64 |psi|^2 partial sums of nvec canonical vectors (count complex-triplet sites each, vector v at
+// base + v * vstride sites); partials[v][kNormParts], then launch_reduce_norms(partials, kNormParts, ...).
+const int kNormParts = 512;
+cudaError_t launch_norm_partials(const void *base, int io_prec, int64_t vstride_sites, int64_t count, int nvec,
+                                 double *partials, cudaStream_t s);
 // Canonical caller vectors (io_prec F64/F32, slices [t_first, t_first + nsl)) -> packed storage.
 cudaError_t launch_pack_vectors(const void *src, int io_prec, int64_t src_vstride_sites, char *dst, int prec,
                                 int64_t dst_vstride, const SubGeom &g, const int L[4], int t_first, int nsl,

@@ -45,7 +45,7 @@ EXPORTS = (
     "tls_create", "tls_destroy", "tls_last_error", "tls_version", "tls_bytes_in_use",
     "tls_load_gauge", "tls_build_twolink", "tls_free_gauge", "tls_export_twolink",
     "tls_export_gauge", "tls_smear", "tls_set_profiling", "tls_get_profile",
-    "tls_set_barrier_budget", "tls_serve_start", "tls_serve_stop", "tls_serve_submit",
+    "tls_set_barrier_budget", "tls_autotune", "tls_tune_set", "tls_serve_start", "tls_serve_stop", "tls_serve_submit",
     "tls_serve_poll", "tls_serve_wait",
 )
 
@@ -58,6 +58,11 @@ class tls_profile(ctypes.Structure):
         ("iter_launches", ctypes.c_int64), ("iter_bytes", ctypes.c_double),
         ("iter_flops", ctypes.c_double), ("kernel", ctypes.c_int), ("vecs_per_thread", ctypes.c_int),
     ]
+
+
+class tls_tune_entry(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("vecs_per_thread", ctypes.c_int), ("threads", ctypes.c_int),
+                ("ms_per_step", ctypes.c_double)]
 
 
 class tls_serve_opts(ctypes.Structure):
@@ -99,6 +104,9 @@ def _load() -> ctypes.CDLL:
         "tls_set_profiling": ([P, I], I),
         "tls_get_profile": ([P, ctypes.POINTER(tls_profile)], I),
         "tls_set_barrier_budget": ([P, I64], I),
+        "tls_autotune": ([P, I64, I, I, I, I, ctypes.POINTER(tls_tune_entry), ctypes.POINTER(tls_tune_entry),
+                          I, ctypes.POINTER(I)], I),
+        "tls_tune_set": ([P, I64, I, I, I, ctypes.POINTER(tls_tune_entry)], I),
         "tls_serve_start": ([P, ctypes.POINTER(tls_serve_opts)], I),
         "tls_serve_stop": ([P], I),
         "tls_serve_submit": ([P, ctypes.POINTER(tls_job), ctypes.POINTER(U64)], I),
@@ -224,6 +232,27 @@ def tls_set_barrier_budget(ctx, polls: int) -> None:
     _check(lib.tls_set_barrier_budget(ctx, int(polls)))
 
 
+def _entry(e):
+    return {"kernel": e.kernel, "vecs_per_thread": e.vecs_per_thread, "threads": e.threads,
+            "ms_per_step": e.ms_per_step}
+
+
+def tls_autotune(ctx, gauge: int, nvec: int, storage: int, timeslice: int = TLS_ALL_T, steps: int = 4):
+    """Returns (best, all candidates) as dicts; the best goes to the context's table."""
+    best = tls_tune_entry()
+    arr = (tls_tune_entry * 32)()
+    n = ctypes.c_int()
+    _check(lib.tls_autotune(ctx, int(gauge), int(nvec), int(storage), int(timeslice), int(steps),
+                            ctypes.byref(best), arr, 32, ctypes.byref(n)))
+    return _entry(best), [_entry(arr[k]) for k in range(min(n.value, 32))]
+
+
+def tls_tune_set(ctx, gauge: int, nvec: int, storage: int, timeslice: int, kernel: int,
+                 vecs_per_thread: int = 1, threads: int = 256) -> None:
+    e = tls_tune_entry(int(kernel), int(vecs_per_thread), int(threads), 0.0)
+    _check(lib.tls_tune_set(ctx, int(gauge), int(nvec), int(storage), int(timeslice), ctypes.byref(e)))
+
+
 def tls_serve_start(ctx, max_slots: int = 64, steps_per_launch: int = 1, use_graphs: int = 1) -> None:
     o = tls_serve_opts(max_slots, steps_per_launch, use_graphs)
     _check(lib.tls_serve_start(ctx, ctypes.byref(o)))
@@ -307,6 +336,12 @@ class Context:
 
     def set_barrier_budget(self, polls):
         return tls_set_barrier_budget(self.h, polls)
+
+    def autotune(self, gauge, nvec, storage, timeslice=TLS_ALL_T, steps=4):
+        return tls_autotune(self.h, gauge, nvec, storage, timeslice, steps)
+
+    def tune_set(self, gauge, nvec, storage, timeslice, kernel, vecs_per_thread=1, threads=256):
+        return tls_tune_set(self.h, gauge, nvec, storage, timeslice, kernel, vecs_per_thread, threads)
 
     def bytes_in_use(self):
         return tls_bytes_in_use(self.h)

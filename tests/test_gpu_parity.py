@@ -338,3 +338,35 @@ def test_large_mrhs_workload_sampled(ctx, T, storage, wprec, recon):
         want = oracle.smear(oracle.twolink(U[t:t + 1].cpu().numpy()), src, w["N"], w["sigma"])
         got = vecs[v, t:t + 1].cpu().numpy().astype(np.complex128)
         assert rel_l2(got, want) <= tol(st, w["N"])
+
+
+def test_autotune_picks_a_working_kernel(ctx, T):
+    dims = (8, 8, 8, 4)
+    U = gauge(dims, "haar", 27)
+    vecs = synth.gaussian_vectors(dims, 5, 28, dtype=torch.complex64)
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.build_twolink(gid, T.TLS_F32, 18)
+    best, cands = ctx.autotune(gid, 5, T.TLS_F32, T.TLS_ALL_T, steps=3)
+    assert len(cands) >= 3 and best["ms_per_step"] == min(c["ms_per_step"] for c in cands)
+    kinds = {c["kernel"] for c in cands}
+    assert {T.TLS_KERNEL_MRHS, T.TLS_KERNEL_PERSISTENT} <= kinds
+    x = vecs.clone().cuda()
+    ctx.set_profiling(True)
+    ctx.smear(gid, x, T.TLS_F32, 5, 6, 1.2)  # AUTO uses the table entry
+    assert ctx.get_profile()["kernel"] == best["kernel"]
+    ctx.set_profiling(False)
+    want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), 6, 1.2)
+    assert max(per_vector_rel_l2(x.cpu().numpy().astype(np.complex128), want)) <= 2e-6 * 6
+    ctx.free_gauge(gid)
+
+
+@pytest.mark.parametrize("nvec", [1, 7, 24, 300])
+def test_interleaved_groups_bitwise_equal_planar(ctx, T, nvec):
+    """Multi-RHS (interleaved, groups of <= 256 vectors) == one vector per launch, bitwise."""
+    dims = (4, 6, 4, 2)
+    U = gauge(dims, "haar", 29)
+    vecs = synth.gaussian_vectors(dims, nvec, 30, dtype=torch.complex64)
+    a, na = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 12, T.TLS_KERNEL_MRHS, 4, 0.9, -1)
+    b, nb = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 12, T.TLS_KERNEL_SINGLE, 4, 0.9, -1)
+    assert np.array_equal(a, b)
+    assert np.array_equal(na, nb)
