@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="16^3x8 lattice, for quick checks only")
     ap.add_argument("--lattice", default=None, help="Lx,Ly,Lz,Lt override (profiling cases)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (planner default)")
+    ap.add_argument("--serving", action="store_true", help="run only the serving benchmark (longer)")
+    ap.add_argument("--serve-jobs", type=int, default=60, help="open-loop jobs of the serving run")
     ap.add_argument("--no-extra", action="store_true", help="skip e2e, cpu baseline and side measurements")
     return ap.parse_args()
 
@@ -205,6 +207,133 @@ def reference_arm(args):
     return 0
 
 
+def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0):
+    """Continuous-batching serving on resident gauge fields (Poisson arrivals).
+
+    Phase 1 keeps 8 jobs in flight to measure the saturation rate X_sat
+    (vectors/s); phase 2 submits n_open jobs at Poisson times with rate
+    0.7 * X_sat / E[nvec] and reports submit->result latency.  The same job
+    stream is then smeared by the plain FP64 one-vector-at-a-time form
+    (tls_smear, TLS_KERNEL_SINGLE, FP64 storage and W) for comparison.
+    """
+    import threading
+    import numpy as np
+    import torch
+    from paper_2301_05518_gb300 import synth, workloads
+    w = workloads.SERVING
+    rng = np.random.default_rng(w["arrival_seed"])
+    torch.manual_seed(w["vec_seed"])
+    ctx = T.Context(device, hbm_cap_bytes=w["hbm_cap"])
+    gids, gids64 = [], []
+    for k, dims in enumerate(w["configs"]):
+        U = synth.gauge_haar(dims, w["gauge_seed"] + k, nd=4, device="cuda")
+        g = ctx.load_gauge(U, 4, dims)
+        ctx.build_twolink(g, T.TLS_F32, T.TLS_R18, keep_U=0)
+        gids.append(g)
+        del U
+    torch.cuda.synchronize()
+
+    def spec():
+        c = int(rng.integers(0, len(w["configs"])))
+        nvec = int(rng.integers(w["nvec"][0], w["nvec"][1] + 1))
+        N = int(rng.integers(w["N"][0], w["N"][1] + 1))
+        sig = N * float(rng.uniform(*w["sigma_per_N"]))
+        st = T.TLS_F32 if rng.random() < 0.5 else T.TLS_F16
+        return c, nvec, N, sig, st
+
+    def vecs_for(c, nvec):
+        Lx, Ly, Lz, Lt = w["configs"][c]
+        return torch.randn((nvec, Lt, Lz, Ly, Lx, 3), dtype=torch.complex64, device="cuda")
+
+    ctx.serve_start(max_slots=48, steps_per_launch=4, use_graphs=1)
+    # phase 1: closed loop
+    t0 = time.perf_counter()
+    pending = []
+    done_vecs = 0
+    specs1 = [spec() for _ in range(n_closed)]
+    it = iter(specs1)
+    while True:
+        while len(pending) < 8:
+            sp = next(it, None)
+            if sp is None:
+                break
+            c, nvec, N, sig, st = sp
+            x = vecs_for(c, nvec)
+            torch.cuda.synchronize()
+            pending.append((ctx.serve_submit(gids[c], x, T.TLS_F32, nvec, N, sig, storage=st), x, nvec))
+        if not pending:
+            break
+        j, x, nvec = pending.pop(0)
+        ctx.serve_wait(j, 600)
+        done_vecs += nvec
+        if time.perf_counter() - t0 > time_cap_s:
+            for j2, _, _ in pending:
+                ctx.serve_wait(j2, 600)
+            pending = []
+            break
+    x_sat = done_vecs / (time.perf_counter() - t0)
+    # phase 2: open-loop Poisson
+    specs2 = [spec() for _ in range(n_open)]
+    mean_nvec = np.mean([s_[1] for s_ in specs2])
+    lam = 0.7 * x_sat / mean_nvec
+    gaps = rng.exponential(1.0 / lam, size=n_open)
+    results = []
+    lock = threading.Lock()
+
+    def waiter(j, nvec, keep):
+        r = ctx.serve_wait(j, 900)
+        with lock:
+            results.append((r, nvec))
+        del keep
+
+    threads = []
+    start = time.perf_counter()
+    tnext = start
+    for (c, nvec, N, sig, st), gap in zip(specs2, gaps):
+        tnext += gap
+        x = vecs_for(c, nvec)
+        torch.cuda.synchronize()
+        now = time.perf_counter()
+        if tnext > now:
+            time.sleep(tnext - now)
+        j = ctx.serve_submit(gids[c], x, T.TLS_F32, nvec, N, sig, storage=st)
+        th = threading.Thread(target=waiter, args=(j, nvec, x))
+        th.start()
+        threads.append(th)
+        if time.perf_counter() - start > time_cap_s:
+            break
+    for th in threads:
+        th.join()
+    ctx.serve_stop()
+    lat = np.array([r["done_ms"] - r["submit_ms"] for r, _ in results])
+    span_s = (max(r["done_ms"] for r, _ in results) - min(r["submit_ms"] for r, _ in results)) / 1e3
+    vec_total = sum(n for _, n in results)
+    out = {"workload": "Poisson jobs on resident 16^3x32, 32^3x64, 48^3x96 Haar fields; 1-24 vectors, "
+                       "N 10-80, sigma/N 0.05-0.3, FP32/FP16 50:50, cap 120 GB",
+           "x_sat_vectors_per_s": x_sat, "rate_jobs_per_s": lam, "jobs": len(results),
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "max_ms": float(lat.max()), "vectors_per_s": vec_total / span_s}
+    # plain FP64 one-vector-at-a-time on the same stream (bounded by time)
+    for k, dims in enumerate(w["configs"]):
+        U = synth.gauge_haar(dims, w["gauge_seed"] + k, nd=4, device="cuda")
+        g = ctx.load_gauge(U, 4, dims)
+        ctx.build_twolink(g, T.TLS_F64, T.TLS_R18, keep_U=0)
+        gids64.append(g)
+        del U
+    t0 = time.perf_counter()
+    v64 = 0
+    for (c, nvec, N, sig, st) in specs2:
+        x = vecs_for(c, nvec).to(torch.complex128)
+        ctx.smear(gids64[c], x, T.TLS_F64, nvec, N, sig, storage=T.TLS_F64, kernel=T.TLS_KERNEL_SINGLE)
+        v64 += nvec
+        if time.perf_counter() - t0 > fp64_cap_s:
+            break
+    out["fp64_one_vector_vectors_per_s"] = v64 / (time.perf_counter() - t0)
+    out["speedup_vs_fp64_one_vector"] = out["vectors_per_s"] / out["fp64_one_vector_vectors_per_s"]
+    ctx.close()
+    return out
+
+
 def our_arm(args):
     import torch
     ws, rank, local = dist_setup("nccl")
@@ -355,6 +484,13 @@ def our_arm(args):
             result["cpu_baseline"] = {"value": vps, "unit": UNIT, "cores": threads, "kind": "oracle",
                                       "sample": "1 of %d vectors on %d of %d slices, all %d steps, FP64 "
                                                 "(twolink + smear), %.1f s" % (nvec, nsl, Lt, N, dt)}
+    if not args.no_extra:
+        del U, vecs
+        torch.cuda.empty_cache()
+        extra["serving"] = serving_run(T, local, n_closed=24, n_open=args.serve_jobs, time_cap_s=25.0,
+                                       fp64_cap_s=10.0)
+        result["serving_p50_ms"] = extra["serving"]["p50_ms"]
+        result["serving_p99_ms"] = extra["serving"]["p99_ms"]
     result["extra"] = extra
     if rank == 0:
         print(json.dumps(result))
@@ -368,6 +504,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.serving:
+        import torch
+        ws, rank, local = dist_setup("nccl")
+        torch.cuda.set_device(local)
+        from paper_2301_05518_gb300 import tls
+        out = serving_run(tls, local, n_closed=48, n_open=args.serve_jobs, time_cap_s=90.0)
+        if rank == 0:
+            print(json.dumps({"metric": "serving p50/p99 ms and vectors/s", "unit": "ms", **out}))
+        return 0
     return our_arm(args)
 
 

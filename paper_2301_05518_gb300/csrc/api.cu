@@ -114,6 +114,14 @@ int default_vb(int storage, int nvec)
     return vb;
 }
 
+int default_il_vb(int storage, int nvec)
+{
+    const int cap = storage == TLS_F64 ? 2 : 4;
+    for (int vb = cap; vb > 1; vb /= 2)
+        if (nvec % vb == 0) return vb;
+    return 1;
+}
+
 cudaError_t launch_step(const StepArgs &a)
 {
     switch (a.prec_in) {
@@ -226,7 +234,7 @@ void tls_destroy(tls_ctx *ctx)
     if (!ctx) return;
     serve_shutdown(ctx);
     {
-        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        std::lock_guard<FairMutex> lk(ctx->mu);
         cudaSetDevice(ctx->device);
         cudaDeviceSynchronize();
         for (auto &kv : ctx->gauges) free_gauge(ctx, kv.second);
@@ -248,7 +256,7 @@ void tls_destroy(tls_ctx *ctx)
 tls_status tls_set_profiling(tls_ctx *ctx, int on)
 {
     if (!ctx) return fail(TLS_ERR_ARG, "tls_set_profiling: ctx is NULL");
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::lock_guard<FairMutex> lk(ctx->mu);
     ctx->profiling = on != 0;
     return ok();
 }
@@ -256,7 +264,7 @@ tls_status tls_set_profiling(tls_ctx *ctx, int on)
 tls_status tls_get_profile(tls_ctx *ctx, tls_profile *out)
 {
     if (!ctx || !out) return fail(TLS_ERR_ARG, "tls_get_profile: NULL argument");
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::lock_guard<FairMutex> lk(ctx->mu);
     *out = ctx->prof;
     return ok();
 }
@@ -264,7 +272,7 @@ tls_status tls_get_profile(tls_ctx *ctx, tls_profile *out)
 tls_status tls_set_barrier_budget(tls_ctx *ctx, int64_t polls)
 {
     if (!ctx || polls < 0) return fail(TLS_ERR_ARG, "tls_set_barrier_budget: bad argument");
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::lock_guard<FairMutex> lk(ctx->mu);
     ctx->barrier_budget = polls;
     return ok();
 }
@@ -283,7 +291,7 @@ tls_status tls_load_gauge(tls_ctx *ctx, const double *U, int nd, const int dims[
                         dims[k]);
     const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
     if (V >= (1LL << 31)) return fail(TLS_ERR_ARG, "tls_load_gauge: %lld sites exceed 2^31", (long long)V);
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::lock_guard<FairMutex> lk(ctx->mu);
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     Gauge gg;
@@ -337,7 +345,7 @@ tls_status tls_load_gauge(tls_ctx *ctx, const double *U, int nd, const int dims[
 tls_status tls_build_twolink(tls_ctx *ctx, tls_gauge_id id, int wprec, int recon, int keep_U, void *stream)
 {
     if (!ctx) return fail(TLS_ERR_ARG, "tls_build_twolink: ctx is NULL");
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::lock_guard<FairMutex> lk(ctx->mu);
     Gauge *gg = find_gauge(ctx, id);
     if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_build_twolink: unknown gauge id %lld", (long long)id);
     if (!gg->Up) return fail(TLS_ERR_STATE, "tls_build_twolink: the links of gauge %lld were released", (long long)id);
@@ -390,7 +398,7 @@ tls_status tls_build_twolink(tls_ctx *ctx, tls_gauge_id id, int wprec, int recon
 tls_status tls_free_gauge(tls_ctx *ctx, tls_gauge_id id)
 {
     if (!ctx) return fail(TLS_ERR_ARG, "tls_free_gauge: ctx is NULL");
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::lock_guard<FairMutex> lk(ctx->mu);
     Gauge *gg = find_gauge(ctx, id);
     if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_free_gauge: unknown gauge id %lld", (long long)id);
     cudaSetDevice(ctx->device);
@@ -405,7 +413,7 @@ tls_status tls_free_gauge(tls_ctx *ctx, tls_gauge_id id)
 static tls_status export_common(tls_ctx *ctx, tls_gauge_id id, double *out, int on_device, void *stream, bool w)
 {
     if (!ctx || !out) return fail(TLS_ERR_ARG, "tls_export: NULL argument");
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::lock_guard<FairMutex> lk(ctx->mu);
     Gauge *gg = find_gauge(ctx, id);
     if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_export: unknown gauge id %lld", (long long)id);
     if (w && !gg->built) return fail(TLS_ERR_NOT_BUILT, "tls_export_twolink: W not built");
@@ -469,7 +477,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     if (!std::isfinite(width)) return fail(TLS_ERR_ARG, "tls_smear: width is not finite");
     if (kernel < TLS_KERNEL_AUTO || kernel > TLS_KERNEL_PERSISTENT)
         return fail(TLS_ERR_ARG, "tls_smear: kernel %d", kernel);
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::lock_guard<FairMutex> lk(ctx->mu);
     Gauge *gg = find_gauge(ctx, id);
     if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_smear: unknown gauge id %lld", (long long)id);
     if (!gg->built) return fail(TLS_ERR_NOT_BUILT, "tls_smear: tls_build_twolink has not run for gauge %lld", (long long)id);
@@ -491,36 +499,36 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     const size_t io_elem = io_prec == TLS_F64 ? 8 : 4;
     const size_t io_slice_bytes = (size_t)Vslice * 6 * io_elem;
 
-    // Kernel choice.
+    // Kernel choice: explicit kernel, or the autotune table, or the planner's default.
     int kern = kernel;
-    int vb = default_vb(storage, nvec);
+    int vb = 0;
     int threads = 0;
-    if (kern == TLS_KERNEL_AUTO) {
+    {
         TuneKey key{{gg->L[0], gg->L[1], gg->L[2], gg->L[3]}, nsl, nvec, storage, gg->wfmt};
         auto it = ctx->tune.find(key);
-        if (it != ctx->tune.end()) {
-            kern = it->second.kernel;
-            vb = it->second.vb;
-            threads = it->second.threads;
-        } else {
-            kern = nvec == 1 ? TLS_KERNEL_SINGLE : TLS_KERNEL_MRHS;
+        const bool have = it != ctx->tune.end();
+        if (kern == TLS_KERNEL_AUTO) {
+            kern = have ? it->second.kernel : (nvec == 1 ? TLS_KERNEL_SINGLE : TLS_KERNEL_MRHS);
         }
-    } else {
-        TuneKey key{{gg->L[0], gg->L[1], gg->L[2], gg->L[3]}, nsl, nvec, storage, gg->wfmt};
-        auto it = ctx->tune.find(key);
-        if (it != ctx->tune.end() && it->second.kernel == kern) {
+        if (have && it->second.kernel == kern) {
             vb = it->second.vb;
             threads = it->second.threads;
         }
     }
     if (force_vb > 0) vb = force_vb;
     if (force_threads > 0) threads = force_threads;
-    if (kern == TLS_KERNEL_SINGLE) vb = 1;
-    if (kern == TLS_KERNEL_PERSISTENT) {
+    const int G0 = std::min(nvec, 256);
+    if (kern == TLS_KERNEL_SINGLE) {
+        vb = 1;
+        if (threads <= 0) threads = 128;
+    } else if (kern == TLS_KERNEL_MRHS) {
+        if (vb <= 0 || vb > 4 || G0 % vb != 0 || (storage == TLS_F64 && vb > 2)) vb = default_il_vb(storage, G0);
         if (threads <= 0) threads = 256;
+    } else {
+        if (vb <= 0) vb = default_vb(storage, nvec);
         if (vb == 2) vb = 1;
+        if (threads <= 0) threads = 256;
     }
-    if (threads <= 0) threads = kern == TLS_KERNEL_MRHS ? 256 : 128;
     // The multi-RHS kernel works on the interleaved layout in groups of <= 256 vectors.
     const int G = kern == TLS_KERNEL_MRHS ? std::min(nvec, 256) : nvec;
 
@@ -746,7 +754,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
                                                  : (double)N * sites * (wb * ((nvec + G - 1) / G) + nvec * vbb);
         p.iter_flops = 450.0 * N * nvec * sites;
         p.kernel = kern;
-        p.vecs_per_thread = kern == TLS_KERNEL_MRHS ? 1 : vb;
+        p.vecs_per_thread = vb;
     }
     if (herr & DERR_TIMEOUT)
         return fail(TLS_ERR_TIMEOUT, "tls_smear: a bounded inter-block barrier of the persistent kernel ran out");

@@ -18,6 +18,41 @@ namespace tls {
 
 struct Server;
 
+// Recursive mutex that grants the lock in arrival order (ticket lock), so a
+// host thread calling into the library is not starved by the serving
+// scheduler re-taking the lock round after round.
+class FairMutex {
+  public:
+    void lock()
+    {
+        std::unique_lock<std::mutex> lk(m_);
+        if (depth_ > 0 && owner_ == std::this_thread::get_id()) {
+            ++depth_;
+            return;
+        }
+        const uint64_t ticket = next_++;
+        cv_.wait(lk, [&] { return serving_ == ticket && depth_ == 0; });
+        owner_ = std::this_thread::get_id();
+        depth_ = 1;
+    }
+    void unlock()
+    {
+        std::unique_lock<std::mutex> lk(m_);
+        if (--depth_ == 0) {
+            owner_ = std::thread::id();
+            ++serving_;
+            cv_.notify_all();
+        }
+    }
+
+  private:
+    std::mutex m_;
+    std::condition_variable cv_;
+    uint64_t next_ = 0, serving_ = 0;
+    std::thread::id owner_;
+    int depth_ = 0;
+};
+
 struct DevBuf {
     void *p = nullptr;
     size_t n = 0;
@@ -59,7 +94,7 @@ struct tls_ctx {
     int num_sms = 0;
     uint64_t cap = 0;                       // 0 = no cap
     std::atomic<uint64_t> used{0};
-    std::recursive_mutex mu;                // serialises device work on this context
+    tls::FairMutex mu;                      // serialises device work on this context
     std::map<int64_t, tls::Gauge> gauges;
     int64_t next_id = 1;
 
@@ -99,6 +134,8 @@ void release(tls_ctx *ctx, DevBuf &b);
 // Shared argument checks for smearing (tls_smear and serving).
 tls_status check_smear_combo(const Gauge &gg, int storage);
 int default_vb(int storage, int nvec);
+// Vectors per thread of the interleaved multi-RHS kernel (a divisor of nvec).
+int default_il_vb(int storage, int nvec);
 
 // tls_smear with an optional forced vectors-per-thread / threads (0 = planner's choice).
 tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec, int N,

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) k_step(const char *__restrict__ W, const 
 // per vector is the same sequence as site_step, so results are bitwise equal
 // to the planar kernels.
 // --------------------------------------------------------------------------
-template <int VP, int WF>
+template <int VP, int WF, int VB, bool A16>
 __global__ void __launch_bounds__(256) k_step_il(const char *__restrict__ W, const char *__restrict__ in,
                                                  char *__restrict__ out, const double *__restrict__ alpha,
                                                  const int *__restrict__ active, SubGeom g, int nvec)
@@ -152,10 +152,17 @@ __global__ void __launch_bounds__(256) k_step_il(const char *__restrict__ W, con
     typedef typename VRec<VP>::R R;
     constexpr int WB = wfmt_bytes(WF);
     constexpr int VBY = vfmt_bytes(VP);
-    const int v = threadIdx.x;
+    const int v0 = threadIdx.x * VB;  // nvec is a multiple of VB
     const int xq = blockIdx.x * blockDim.y + threadIdx.y;
     if (xq >= g.hx) return;
-    if (active != nullptr && active[v] == 0) return;
+    bool on[VB];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < VB; ++k) {
+        on[k] = active == nullptr || active[v0 + k] != 0;
+        any = any || on[k];
+    }
+    if (!any) return;
     const int yq = blockIdx.y;
     const int blk = blockIdx.z / g.hz;
     const int zq = blockIdx.z - blk * g.hz;
@@ -169,29 +176,54 @@ __global__ void __launch_bounds__(256) k_step_il(const char *__restrict__ W, con
     fw[2] = zq == g.hz - 1 ? i - (g.hz - 1) * sz : i + sz;
     bw[2] = zq == 0 ? i + (g.hz - 1) * sz : i - sz;
     const char *wb = W + (int64_t)blk * 3 * g.Ps * WB;
-    const int64_t base = (int64_t)blk * g.Ps;
-    cpx<R> acc[3];
+    // records of this block, vectors v0.. of site s at rin + s * nvec * VBY
+    const char *rin = in + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
+    char *rout = out + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
+    const unsigned rstride = (unsigned)nvec * VBY;
+    cpx<R> acc[VB][3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c].re = acc[c].im = R(0);
+    for (int k = 0; k < VB; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[k][c].re = acc[k][c].im = R(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        cpx<R> m[9], p[3];
+        cpx<R> m[9], p[VB][3];
         WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, i, m);
-        VRec<VP>::load(in + ((base + fw[d]) * nvec + v) * VBY, p);
-        mv_add(m, p, acc);
-        WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, bw[d], m);
-        VRec<VP>::load(in + ((base + bw[d]) * nvec + v) * VBY, p);
-        mdv_add(m, p, acc);
-    }
-    cpx<R> c[3], o[3];
-    VRec<VP>::load(in + ((base + i) * nvec + v) * VBY, c);
-    const R a = (R)alpha[v];
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)fw[d] * rstride, p);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        o[k].re = fma(a, fma(R(-6), c[k].re, acc[k].re), c[k].re);
-        o[k].im = fma(a, fma(R(-6), c[k].im, acc[k].im), c[k].im);
+        for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
+        WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, bw[d], m);
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)bw[d] * rstride, p);
+#pragma unroll
+        for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
     }
-    VRec<VP>::store(out + ((base + i) * nvec + v) * VBY, o);
+    cpx<R> c[VB][3], o[VB][3];
+    RecGroup<VP, VB, A16>::load(rin + (unsigned)i * rstride, c);
+#pragma unroll
+    for (int k = 0; k < VB; ++k) {
+        const R a = (R)alpha[v0 + k];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            o[k][q].re = fma(a, fma(R(-6), c[k][q].re, acc[k][q].re), c[k][q].re);
+            o[k][q].im = fma(a, fma(R(-6), c[k][q].im, acc[k][q].im), c[k][q].im);
+        }
+        if (!on[k]) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) o[k][q] = c[k][q];
+        }
+    }
+    if (VB == 1 || (on[0] && on[VB - 1] && [&] {
+            bool all = true;
+#pragma unroll
+            for (int k = 0; k < VB; ++k) all = all && on[k];
+            return all;
+        }())) {
+        RecGroup<VP, VB, A16>::store(rout + (unsigned)i * rstride, o);
+    } else {
+#pragma unroll
+        for (int k = 0; k < VB; ++k)
+            if (on[k]) VRec<VP>::store(rout + (unsigned)i * rstride + k * VBY, o[k]);
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -351,23 +383,45 @@ inline int il_spb(int nvec, int threads)
     return spb;
 }
 
-template <int VP, int WF> cudaError_t step_il_launch(const StepArgs &a)
+template <int VP, int WF, int VB, bool A16> cudaError_t step_il_launch(const StepArgs &a)
 {
-    if (a.nvec < 1 || a.nvec > 256) return cudaErrorInvalidValue;
-    const int spb = il_spb(a.nvec, a.threads);
-    dim3 block(a.nvec, spb);
+    const int tx = a.nvec / VB;
+    const int spb = il_spb(tx, a.threads);
+    dim3 block(tx, spb);
     dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    k_step_il<VP, WF><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g, a.nvec);
+    k_step_il<VP, WF, VB, A16><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g, a.nvec);
     return cudaGetLastError();
 }
 
+// vb = vectors per thread; it must divide nvec (else 1 is used).  FP32 groups
+// of an even count on an even nvec are 16-byte aligned.
 template <int VP, int WF> cudaError_t step_il_w(const StepArgs &a)
 {
-    if constexpr (!combo_ok<VP, WF>())
+    if constexpr (!combo_ok<VP, WF>()) {
         return cudaErrorNotSupported;
-    else
-        return step_il_launch<VP, WF>(a);
+    } else {
+        if (a.nvec < 1 || a.nvec > 256) return cudaErrorInvalidValue;
+        int vb = a.vb > 0 ? a.vb : 1;
+        if (a.nvec % vb != 0) vb = 1;
+        if constexpr (VP == P_F32) {
+            const bool a16 = (a.nvec % 2 == 0);
+            switch (vb) {
+            case 2: return a16 ? step_il_launch<VP, WF, 2, true>(a) : step_il_launch<VP, WF, 2, false>(a);
+            case 4: return a16 ? step_il_launch<VP, WF, 4, true>(a) : step_il_launch<VP, WF, 4, false>(a);
+            default: return step_il_launch<VP, WF, 1, false>(a);
+            }
+        } else if constexpr (VP == P_F64) {
+            if (vb == 2) return step_il_launch<VP, WF, 2, false>(a);
+            return step_il_launch<VP, WF, 1, false>(a);
+        } else {
+            switch (vb) {
+            case 2: return step_il_launch<VP, WF, 2, false>(a);
+            case 4: return step_il_launch<VP, WF, 4, false>(a);
+            default: return step_il_launch<VP, WF, 1, false>(a);
+            }
+        }
+    }
 }
 
 template <int VP, int WF> cudaError_t step_w(const StepArgs &a)

@@ -136,7 +136,7 @@ tls_status make_batch(tls_ctx *ctx, Server *sv, const BatchKey &key, const Gauge
     b->key = key;
     b->S = sv->opts.max_slots;
     b->K = sv->opts.steps_per_launch;
-    b->vb = default_vb(key.storage, b->S);
+    b->vb = default_il_vb(key.storage, b->S);
     b->nsl = key.timeslice < 0 ? gg.L[3] : 1;
     b->t_first = key.timeslice < 0 ? 0 : key.timeslice;
     b->nblk = b->nsl * 8;
@@ -422,29 +422,43 @@ void scheduler(tls_ctx *ctx, Server *sv)
             waiting.assign(sv->pending.begin(), sv->pending.end());
             sv->pending.clear();
         }
-        std::lock_guard<std::recursive_mutex> g(ctx->mu);
-        std::vector<Job *> keep;
-        for (Job *j : waiting)
-            if (try_admit(ctx, sv, j)) keep.push_back(j);
-        if (!keep.empty()) {
-            std::lock_guard<std::mutex> lk(sv->m);
-            sv->pending.insert(sv->pending.begin(), keep.begin(), keep.end());
-        }
-        for (auto &kv : sv->batches) {
-            Batch *b = kv.second.get();
-            if (b->active_slots() == 0) continue;
-            cudaError_t e = launch_round(ctx, sv, b);
-            if (e != cudaSuccess) fail_batch(ctx, sv, b, cuda_fail(e, "serve: round"));
-        }
-        for (auto &kv : sv->batches) {
-            Batch *b = kv.second.get();
-            if (b->used_slots() == 0) continue;
-            cudaError_t e = cudaStreamSynchronize(b->stream);
-            if (e != cudaSuccess) {
-                fail_batch(ctx, sv, b, cuda_fail(e, "serve: round"));
-                continue;
+        std::vector<Batch *> running;
+        {
+            std::lock_guard<FairMutex> g(ctx->mu);
+            std::vector<Job *> keep;
+            for (Job *j : waiting)
+                if (try_admit(ctx, sv, j)) keep.push_back(j);
+            if (!keep.empty()) {
+                std::lock_guard<std::mutex> lk(sv->m);
+                sv->pending.insert(sv->pending.begin(), keep.begin(), keep.end());
             }
-            retire(ctx, sv, b);
+            for (auto &kv : sv->batches) {
+                Batch *b = kv.second.get();
+                if (b->used_slots() == 0) continue;
+                if (b->active_slots() > 0) {
+                    cudaError_t e = launch_round(ctx, sv, b);
+                    if (e != cudaSuccess) {
+                        fail_batch(ctx, sv, b, cuda_fail(e, "serve: round"));
+                        continue;
+                    }
+                }
+                running.push_back(b);
+            }
+        }
+        // Wait for the device without holding the context lock: other host
+        // threads may call into the library meanwhile.  Batches with slots in
+        // use are never destroyed outside this thread.
+        std::vector<cudaError_t> status(running.size());
+        for (size_t k = 0; k < running.size(); ++k) status[k] = cudaStreamSynchronize(running[k]->stream);
+        {
+            std::lock_guard<FairMutex> g(ctx->mu);
+            for (size_t k = 0; k < running.size(); ++k) {
+                if (status[k] != cudaSuccess) {
+                    fail_batch(ctx, sv, running[k], cuda_fail(status[k], "serve: round"));
+                    continue;
+                }
+                retire(ctx, sv, running[k]);
+            }
         }
     }
 }
@@ -461,7 +475,7 @@ void serve_shutdown(tls_ctx *ctx)
         sv->cv_work.notify_all();
     }
     if (sv->th.joinable()) sv->th.join();
-    std::lock_guard<std::recursive_mutex> g(ctx->mu);
+    std::lock_guard<FairMutex> g(ctx->mu);
     for (auto &kv : sv->batches) {
         fail_batch(ctx, sv, kv.second.get(), fail(TLS_ERR_STATE, "serve: stopped"));
         destroy_batch(ctx, kv.second.get());
@@ -477,11 +491,11 @@ bool serve_gauge_busy(tls_ctx *ctx, int64_t id)
 {
     Server *sv = ctx->server;
     if (!sv) return false;
-    {
-        std::lock_guard<std::mutex> lk(sv->m);
-        for (Job *j : sv->pending)
-            if (j->d.gauge == id) return true;
-    }
+    // The caller holds ctx->mu, so the scheduler is not admitting or launching;
+    // sv->m keeps its idle check (any_busy) off the map while it changes.
+    std::lock_guard<std::mutex> lk(sv->m);
+    for (Job *j : sv->pending)
+        if (j->d.gauge == id) return true;
     for (auto it = sv->batches.begin(); it != sv->batches.end();) {
         Batch *b = it->second.get();
         if (b->key.gauge == id) {
@@ -504,7 +518,7 @@ extern "C" {
 tls_status tls_serve_start(tls_ctx *ctx, const tls_serve_opts *opts)
 {
     if (!ctx) return fail(TLS_ERR_ARG, "tls_serve_start: ctx is NULL");
-    std::lock_guard<std::recursive_mutex> g(ctx->mu);
+    std::lock_guard<FairMutex> g(ctx->mu);
     if (ctx->server) return fail(TLS_ERR_STATE, "tls_serve_start: already serving");
     std::unique_ptr<Server> sv(new Server());
     sv->opts.max_slots = 64;
@@ -542,7 +556,7 @@ tls_status tls_serve_submit(tls_ctx *ctx, const tls_job *job, uint64_t *job_id)
     if (job->nvec > sv->opts.max_slots)
         return fail(TLS_ERR_ARG, "tls_serve_submit: nvec %d exceeds max_slots %d", job->nvec, sv->opts.max_slots);
     {
-        std::lock_guard<std::recursive_mutex> g(ctx->mu);
+        std::lock_guard<FairMutex> g(ctx->mu);
         auto it = ctx->gauges.find(job->gauge);
         if (it == ctx->gauges.end()) return fail(TLS_ERR_NOT_FOUND, "tls_serve_submit: unknown gauge");
         const Gauge &gg = it->second;

@@ -455,6 +455,58 @@ template <typename H> struct VRecH {
 template <> struct VRec<P_F16> : VRecH<__half> {};
 template <> struct VRec<P_BF16> : VRecH<__nv_bfloat16> {};
 
+// VB adjacent interleaved records (vectors v0 .. v0+VB-1 of one site).  With
+// A16 the group starts on a 16-byte boundary and is read with 16-byte loads
+// (FP32: 24*VB bytes = 1.5*VB words; needs VB even).
+template <int VP, int VB, bool A16> struct RecGroup {
+    typedef typename VRec<VP>::R R;
+    static __device__ __forceinline__ void load(const char *p, cpx<R> v[VB][3])
+    {
+#pragma unroll
+        for (int k = 0; k < VB; ++k) VRec<VP>::load(p + k * vfmt_bytes(VP), v[k]);
+    }
+    static __device__ __forceinline__ void store(char *p, const cpx<R> v[VB][3])
+    {
+#pragma unroll
+        for (int k = 0; k < VB; ++k) VRec<VP>::store(p + k * vfmt_bytes(VP), v[k]);
+    }
+};
+
+template <int VB> struct RecGroup<P_F32, VB, true> {
+    static_assert(VB % 2 == 0, "16-byte FP32 record groups need an even count");
+    static __device__ __forceinline__ void load(const char *p, cpx<float> v[VB][3])
+    {
+        const float4 *q = reinterpret_cast<const float4 *>(p);
+        float f[6 * VB];
+#pragma unroll
+        for (int k = 0; k < 3 * VB / 2; ++k) {
+            float4 a = q[k];
+            f[4 * k] = a.x; f[4 * k + 1] = a.y; f[4 * k + 2] = a.z; f[4 * k + 3] = a.w;
+        }
+#pragma unroll
+        for (int k = 0; k < VB; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[k][c].re = f[6 * k + 2 * c];
+                v[k][c].im = f[6 * k + 2 * c + 1];
+            }
+    }
+    static __device__ __forceinline__ void store(char *p, const cpx<float> v[VB][3])
+    {
+        float f[6 * VB];
+#pragma unroll
+        for (int k = 0; k < VB; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                f[6 * k + 2 * c] = v[k][c].re;
+                f[6 * k + 2 * c + 1] = v[k][c].im;
+            }
+        float4 *q = reinterpret_cast<float4 *>(p);
+#pragma unroll
+        for (int k = 0; k < 3 * VB / 2; ++k) q[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+    }
+};
+
 // The six +-1 sublattice neighbours of site i (periodic in h).
 __device__ __forceinline__ void sub_neighbours(const SubGeom &g, int i, int fw[3], int bw[3])
 {

@@ -6,6 +6,7 @@
 // then uses it.  Candidates: the one-vector-per-launch kernel, the
 // interleaved multi-RHS kernel at several CTA sizes, and the persistent
 // kernel at several vectors-per-thread.
+#include <algorithm>
 #include <cstring>
 
 #include "api_internal.h"
@@ -25,8 +26,12 @@ std::vector<Cand> candidates(int nvec, int storage)
         c.push_back({TLS_KERNEL_SINGLE, 1, 128});
         c.push_back({TLS_KERNEL_SINGLE, 1, 256});
     }
-    for (int t : {64, 128, 256})
-        if (t >= nvec || t == 256) c.push_back({TLS_KERNEL_MRHS, 1, t});
+    const int G = std::min(nvec, 256);
+    for (int vb : {1, 2, 4}) {
+        if (G % vb != 0 || (storage == TLS_F64 && vb > 2)) continue;
+        for (int t : {64, 128, 256})
+            if (t >= G / vb || t == 256) c.push_back({TLS_KERNEL_MRHS, vb, t});
+    }
     const int vmax = storage == TLS_F64 ? 4 : 8;
     for (int vb : {1, 4, 8})
         if (vb <= vmax && (vb == 1 || vb <= 2 * nvec)) c.push_back({TLS_KERNEL_PERSISTENT, vb, 256});
@@ -47,7 +52,7 @@ tls_status tls_tune_set(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
     if (!ctx || !entry) return fail(TLS_ERR_ARG, "tls_tune_set: NULL argument");
     if (entry->kernel < TLS_KERNEL_SINGLE || entry->kernel > TLS_KERNEL_PERSISTENT)
         return fail(TLS_ERR_ARG, "tls_tune_set: kernel %d", entry->kernel);
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::lock_guard<FairMutex> lk(ctx->mu);
     auto it = ctx->gauges.find(id);
     if (it == ctx->gauges.end()) return fail(TLS_ERR_NOT_FOUND, "tls_tune_set: unknown gauge");
     const Gauge &gg = it->second;
@@ -63,7 +68,7 @@ tls_status tls_autotune(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
 {
     if (!ctx) return fail(TLS_ERR_ARG, "tls_autotune: ctx is NULL");
     if (nvec < 1 || steps < 1) return fail(TLS_ERR_ARG, "tls_autotune: nvec %d, steps %d", nvec, steps);
-    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    std::lock_guard<FairMutex> lk(ctx->mu);
     auto it = ctx->gauges.find(id);
     if (it == ctx->gauges.end()) return fail(TLS_ERR_NOT_FOUND, "tls_autotune: unknown gauge");
     const Gauge gg = it->second;
