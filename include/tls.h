@@ -163,6 +163,29 @@ tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec,
                      int vecs_on_device, int nvec, int N, double width, int timeslice,
                      int storage, int kernel, void *stream, double *norms_out);
 
+/* ---- smearing without any device allocation --------------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory while they run: code in the middle of a
+ * CUDA stream capture (cudaMalloc and cudaFree are not allowed there), a
+ * latency-critical host thread (cudaFree synchronises the whole device), or a
+ * process whose device memory belongs to another allocator.
+ * It computes what tls_smear(..., kernel = TLS_KERNEL_PERSISTENT, ...) does,
+ * on device vectors only (`vecs` is device memory of the context's device,
+ * canonical layout, smeared in place), and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  All its intermediate data lives in one static
+ * device array of TLS_NOALLOC_SCRATCH_BYTES that every device loading the
+ * library holds until the process exits; a smear whose packed vectors and
+ * persistent-kernel scratch do not fit is rejected with TLS_ERR_ARG (use
+ * tls_smear for it).  The first call on a device looks up the array's device
+ * address with that device current, so make that first call before any
+ * stream capture.  Calls share the array: each clears what must start at
+ * zero, and calls whose work overlaps on the GPU race on it.  The gauge must
+ * already be built (tls_build_twolink allocates W; this call does not).
+ * Synchronous on `stream`.  Errors as tls_smear.                            */
+#define TLS_NOALLOC_SCRATCH_BYTES (32u << 20)
+tls_status tls_smear_noalloc(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int nvec, int N,
+                             double width, int timeslice, int storage, void *stream);
+
 /* ---- per-call profile ------------------------------------------------------
  * With profiling on (tls_set_profiling), each tls_smear / tls_build_twolink
  * records CUDA events on its stream around its phases.                     */

@@ -45,7 +45,7 @@ EXPORTS = (
     "tls_create", "tls_destroy", "tls_last_error", "tls_version", "tls_bytes_in_use",
     "tls_load_gauge", "tls_build_twolink", "tls_free_gauge", "tls_export_twolink",
     "tls_export_gauge", "tls_smear", "tls_set_profiling", "tls_get_profile",
-    "tls_set_barrier_budget", "tls_autotune", "tls_tune_set", "tls_serve_start", "tls_serve_stop", "tls_serve_submit",
+    "tls_smear_noalloc", "tls_set_barrier_budget", "tls_autotune", "tls_tune_set", "tls_serve_start", "tls_serve_stop", "tls_serve_submit",
     "tls_serve_poll", "tls_serve_wait",
 )
 
@@ -101,6 +101,7 @@ def _load() -> ctypes.CDLL:
         "tls_export_twolink": ([P, I64, P, I, P], I),
         "tls_export_gauge": ([P, I64, P, I, P], I),
         "tls_smear": ([P, I64, P, I, I, I, I, D, I, I, I, P, P], I),
+        "tls_smear_noalloc": ([P, I64, P, I, I, I, D, I, I, P], I),
         "tls_set_profiling": ([P, I], I),
         "tls_get_profile": ([P, ctypes.POINTER(tls_profile)], I),
         "tls_set_barrier_budget": ([P, I64], I),
@@ -218,6 +219,14 @@ def tls_smear(ctx, gauge: int, vecs, io_prec: int, nvec: int, N: int, width: flo
     return nout
 
 
+def tls_smear_noalloc(ctx, gauge: int, vecs, io_prec: int, nvec: int, N: int, width: float,
+                      timeslice: int = TLS_ALL_T, storage: int = TLS_F32, stream=None) -> None:
+    """The persistent smear with the library's static scratch: allocates nothing."""
+    p, on_dev = _ptr(vecs)
+    _check(lib.tls_smear_noalloc(ctx, int(gauge), p, int(io_prec), int(nvec), int(N), float(width),
+                                 int(timeslice), int(storage), _stream(stream)))
+
+
 def tls_set_profiling(ctx, on: bool = True) -> None:
     _check(lib.tls_set_profiling(ctx, 1 if on else 0))
 
@@ -327,6 +336,10 @@ class Context:
               kernel=TLS_KERNEL_AUTO, stream=None, norms=False):
         return tls_smear(self.h, gauge, vecs, io_prec, nvec, N, width, timeslice, storage, kernel,
                          stream, norms)
+
+    def smear_noalloc(self, gauge, vecs, io_prec, nvec, N, width, timeslice=TLS_ALL_T, storage=TLS_F32,
+                      stream=None):
+        return tls_smear_noalloc(self.h, gauge, vecs, io_prec, nvec, N, width, timeslice, storage, stream)
 
     def set_profiling(self, on=True):
         return tls_set_profiling(self.h, on)
