@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "single", "mrhs", "persistent"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "single", "mrhs", "persistent", "rows"])
     ap.add_argument("--small", action="store_true", help="16^3x8 lattice, for quick checks only")
     ap.add_argument("--lattice", default=None, help="Lx,Ly,Lz,Lt override (profiling cases)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (planner default)")
@@ -347,7 +347,7 @@ def our_arm(args):
     storage = {"f32": T.TLS_F32, "f16": T.TLS_F16, "bf16": T.TLS_BF16}[args.storage]
     wprec = T.TLS_F32
     kernel = {"auto": T.TLS_KERNEL_AUTO, "single": T.TLS_KERNEL_SINGLE, "mrhs": T.TLS_KERNEL_MRHS,
-              "persistent": T.TLS_KERNEL_PERSISTENT}[args.kernel]
+              "persistent": T.TLS_KERNEL_PERSISTENT, "rows": T.TLS_KERNEL_MRHS_ROWS}[args.kernel]
     N, sigma, nvec = w["N"], w["sigma"], w["nvec"]
     hbm_peak, peak_kind = load_peaks()
 
@@ -365,7 +365,7 @@ def our_arm(args):
         ctx.build_twolink(gid, wprec, T.TLS_R18, keep_U=0, stream=stream)
         best, cands = ctx.autotune(gid, nvec, storage, T.TLS_ALL_T, steps=4)
         ctx.free_gauge(gid)
-        names = {1: "single", 2: "mrhs", 3: "persistent"}
+        names = {1: "single", 2: "mrhs", 3: "persistent", 4: "mrhs_rows"}
         tune = {"best": dict(best, kernel=names[best["kernel"]]),
                 "candidates": [dict(c, kernel=names[c["kernel"]]) for c in cands]}
 
@@ -414,10 +414,11 @@ def our_arm(args):
     per_launch_ms = mean_iter_ms / max(1, iter_launches)
     per_launch_bytes = prof_last["iter_bytes"] / max(1, iter_launches)
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
-    kern_name = {1: "single", 2: "mrhs", 3: "persistent"}.get(prof_last["kernel"], "?")
+    kern_name = {1: "single", 2: "mrhs", 3: "persistent", 4: "mrhs_rows"}.get(prof_last["kernel"], "?")
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": None,
-            "kernel": "k_%s" % ("persist" if kern_name == "persistent" else "step"),
+            "kernel": {"persistent": "k_persist", "mrhs": "k_step_il", "mrhs_rows": "k_step_rows",
+                       "single": "k_step"}.get(kern_name, "?"),
             "peak_source": peak_kind,
             "note": ("algorithmic bytes = W once + psi read once + psi written once per site and "
                      "step; persistent launches count all N steps (effective GB/s)")}
@@ -467,12 +468,22 @@ def our_arm(args):
         ctx.build_twolink(gid, T.TLS_F32, T.TLS_R18, keep_U=0, stream=stream)
         x1 = vecs[:1].clone()
         single = {}
-        for kname, kk in (("mrhs", T.TLS_KERNEL_MRHS), ("persistent", T.TLS_KERNEL_PERSISTENT)):
+        for kname, kk in (("single", T.TLS_KERNEL_SINGLE), ("persistent", T.TLS_KERNEL_PERSISTENT)):
             ctx.smear(gid, x1, T.TLS_F32, 1, 20, 4.0, storage=T.TLS_F32, kernel=kk, stream=stream)
             p = ctx.get_profile()
             gbs = p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9
             single[kname] = {"gbs": gbs, "frac": gbs / hbm_peak, "ms_per_step": p["ms_iter"] / 20}
         extra["single_rhs_f32_N20"] = single
+        # the same 24-vector workload with 16-bit storage (per-site scale, FP32 arithmetic)
+        if storage != T.TLS_F16:
+            best16, _ = ctx.autotune(gid, nvec, T.TLS_F16, T.TLS_ALL_T, steps=4)
+            x16 = vecs.clone()
+            ctx.smear(gid, x16, T.TLS_F32, nvec, N, sigma, storage=T.TLS_F16, stream=stream)
+            p = ctx.get_profile()
+            extra["f16_storage"] = {"vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3),
+                                    "ms_per_step": p["ms_iter"] / N, "kernel": best16,
+                                    "gbs": p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9}
+            del x16
         ctx.free_gauge(gid)
         if rank == 0 and ws >= 1:
             # CPU baseline: the oracle on a bounded sample, on this machine's host cores

@@ -75,6 +75,9 @@ typedef int tls_status;
 #define TLS_KERNEL_MRHS       2  /* all vectors in one launch: W read once     */
 #define TLS_KERNEL_PERSISTENT 3  /* all N steps in one cooperative launch,     */
                                  /* tiles kept L2-resident between steps       */
+#define TLS_KERNEL_MRHS_ROWS  4  /* multi-RHS, rows staged in shared memory by */
+                                 /* TMA bulk copies (falls back to MRHS when   */
+                                 /* the shape does not allow 16-byte copies)   */
 
 #define TLS_ALL_T (-1)           /* timeslice argument: smear every slice      */
 

@@ -144,6 +144,16 @@ cudaError_t launch_step_il(const StepArgs &a)
     }
 }
 
+cudaError_t launch_step_rows(const StepArgs &a, int *err)
+{
+    switch (a.prec_in) {
+    case P_F32: return launch_step_rows_f32(a, err);
+    case P_F16: return launch_step_rows_f16(a, err);
+    case P_BF16: return launch_step_rows_bf16(a, err);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 cudaError_t launch_persistent(const PersistArgs &a)
 {
     switch (a.prec) {
@@ -210,6 +220,7 @@ tls_status tls_create(tls_ctx **out, int device, uint64_t hbm_cap_bytes)
     ctx->device = device;
     ctx->cap = hbm_cap_bytes;
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     tls_status s = dev_alloc(ctx.get(), (void **)&ctx->d_err, 256, "tls_create: error word");
     if (s != TLS_OK) return s;
     s = dev_alloc(ctx.get(), (void **)&ctx->d_bar, 256, "tls_create: barrier words");
@@ -475,7 +486,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     if (nvec < 1 || nvec > 65535) return fail(TLS_ERR_ARG, "tls_smear: nvec = %d", nvec);
     if (N < 0) return fail(TLS_ERR_ARG, "tls_smear: N = %d < 0", N);
     if (!std::isfinite(width)) return fail(TLS_ERR_ARG, "tls_smear: width is not finite");
-    if (kernel < TLS_KERNEL_AUTO || kernel > TLS_KERNEL_PERSISTENT)
+    if (kernel < TLS_KERNEL_AUTO || kernel > TLS_KERNEL_MRHS_ROWS)
         return fail(TLS_ERR_ARG, "tls_smear: kernel %d", kernel);
     std::lock_guard<FairMutex> lk(ctx->mu);
     Gauge *gg = find_gauge(ctx, id);
@@ -521,16 +532,22 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     if (kern == TLS_KERNEL_SINGLE) {
         vb = 1;
         if (threads <= 0) threads = 128;
-    } else if (kern == TLS_KERNEL_MRHS) {
+    } else if (kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS) {
         if (vb <= 0 || vb > 4 || G0 % vb != 0 || (storage == TLS_F64 && vb > 2)) vb = default_il_vb(storage, G0);
         if (threads <= 0) threads = 256;
+        // TMA row staging needs 16-byte copies and a row that fits in shared memory
+        if (kern == TLS_KERNEL_MRHS_ROWS &&
+            !(rows_applicable(gg->wfmt, storage, gg->g, G0, vb, ctx->max_smem) &&
+              rows_applicable(gg->wfmt, storage, gg->g, nvec % G0 ? nvec % G0 : G0, vb, ctx->max_smem)))
+            kern = TLS_KERNEL_MRHS;
     } else {
         if (vb <= 0) vb = default_vb(storage, nvec);
         if (vb == 2) vb = 1;
         if (threads <= 0) threads = 256;
     }
     // The multi-RHS kernel works on the interleaved layout in groups of <= 256 vectors.
-    const int G = kern == TLS_KERNEL_MRHS ? std::min(nvec, 256) : nvec;
+    const bool il_layout = kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS;
+    const int G = il_layout ? std::min(nvec, 256) : nvec;
 
     // Workspace.
     size_t a_bytes = (size_t)vs * G;
@@ -634,7 +651,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         const int gn = std::min(G, nvec - g0);
         const char *src_g = src_io + (size_t)g0 * io_vec_bytes;
         char *dst_g = dst_io + (size_t)g0 * io_vec_bytes;
-        const bool il = kern == TLS_KERNEL_MRHS;
+        const bool il = il_layout;
         mark(2);
         e = il ? launch_pack_il(src_g, io_prec, io_vstride_sites, (char *)ctx->A.p, storage, g, gg->L, t_rel, nsl, gn,
                                     gn, 0, st)
@@ -690,7 +707,9 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
                         sa.in = (it & 1) ? y : x;
                         sa.out = (it & 1) ? x : y;
                         sa.alpha = alpha_g + gi;
-                        e = il ? launch_step_il(sa) : launch_step(sa);
+                        e = kern == TLS_KERNEL_MRHS_ROWS ? launch_step_rows(sa, ctx->d_err)
+                            : il                         ? launch_step_il(sa)
+                                                         : launch_step(sa);
                         ++launches;
                         ++iter_launches;
                     }
@@ -757,7 +776,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         p.vecs_per_thread = vb;
     }
     if (herr & DERR_TIMEOUT)
-        return fail(TLS_ERR_TIMEOUT, "tls_smear: a bounded inter-block barrier of the persistent kernel ran out");
+        return fail(TLS_ERR_TIMEOUT, "tls_smear: a bounded device wait (barrier or copy completion) ran out");
     if (herr) return fail(TLS_ERR_DEVICE, "tls_smear: device error word 0x%x", herr);
     if (norms_out) std::memcpy(norms_out, ctx->h_norms, sizeof(double) * nvec);
     return ok();

@@ -92,6 +92,7 @@ struct TuneVal {
 struct tls_ctx {
     int device = 0;
     int num_sms = 0;
+    int max_smem = 0;                       // opt-in shared memory per CTA (bytes)
     uint64_t cap = 0;                       // 0 = no cap
     std::atomic<uint64_t> used{0};
     tls::FairMutex mu;                      // serialises device work on this context

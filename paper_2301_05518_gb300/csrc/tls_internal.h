@@ -52,6 +52,11 @@ struct PersistArgs {
 cudaError_t launch_step(const StepArgs &a);
 // Interleaved-layout multi-RHS step (nvec <= 256 vectors per record group).
 cudaError_t launch_step_il(const StepArgs &a);
+// The same step with TMA row staging in shared memory (k_rows.cuh); err gets
+// DERR_TIMEOUT if a bounded wait runs out.  rows_applicable says whether the
+// shape and formats allow it (16-byte bulk copies, CTA size, shared memory).
+cudaError_t launch_step_rows(const StepArgs &a, int *err);
+bool rows_applicable(int wfmt, int prec, const SubGeom &g, int nvec, int vb, int max_smem);
 cudaError_t launch_persistent(const PersistArgs &a);
 // Co-resident CTAs per SM of the persistent kernel for this combination (0: none).
 int persistent_occupancy(int wfmt, int prec, int sprec, int vb, int threads);
@@ -65,6 +70,10 @@ cudaError_t launch_step_il_f64(const StepArgs &a);
 cudaError_t launch_step_il_f32(const StepArgs &a);
 cudaError_t launch_step_il_f16(const StepArgs &a);
 cudaError_t launch_step_il_bf16(const StepArgs &a);
+cudaError_t launch_step_rows_f64(const StepArgs &a, int *err);
+cudaError_t launch_step_rows_f32(const StepArgs &a, int *err);
+cudaError_t launch_step_rows_f16(const StepArgs &a, int *err);
+cudaError_t launch_step_rows_bf16(const StepArgs &a, int *err);
 cudaError_t launch_persistent_f64(const PersistArgs &a);
 cudaError_t launch_persistent_f32(const PersistArgs &a);
 cudaError_t launch_persistent_f16(const PersistArgs &a);

@@ -19,7 +19,7 @@ struct Cand {
     int kernel, vb, threads;
 };
 
-std::vector<Cand> candidates(int nvec, int storage)
+std::vector<Cand> candidates(int nvec, int storage, bool rows)
 {
     std::vector<Cand> c;
     if (nvec <= 4) {
@@ -31,6 +31,7 @@ std::vector<Cand> candidates(int nvec, int storage)
         if (G % vb != 0 || (storage == TLS_F64 && vb > 2)) continue;
         for (int t : {64, 128, 256})
             if (t >= G / vb || t == 256) c.push_back({TLS_KERNEL_MRHS, vb, t});
+        if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0});
     }
     const int vmax = storage == TLS_F64 ? 4 : 8;
     for (int vb : {1, 4, 8})
@@ -50,7 +51,7 @@ tls_status tls_tune_set(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
                         const tls_tune_entry *entry)
 {
     if (!ctx || !entry) return fail(TLS_ERR_ARG, "tls_tune_set: NULL argument");
-    if (entry->kernel < TLS_KERNEL_SINGLE || entry->kernel > TLS_KERNEL_PERSISTENT)
+    if (entry->kernel < TLS_KERNEL_SINGLE || entry->kernel > TLS_KERNEL_MRHS_ROWS)
         return fail(TLS_ERR_ARG, "tls_tune_set: kernel %d", entry->kernel);
     std::lock_guard<FairMutex> lk(ctx->mu);
     auto it = ctx->gauges.find(id);
@@ -88,7 +89,11 @@ tls_status tls_autotune(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
     ctx->profiling = true;
     TuneVal win{0, 0, 0, 1e300};
     int n = 0;
-    for (const Cand &c : candidates(nvec, storage)) {
+    const int G = std::min(nvec, 256);
+    const bool rows = storage != TLS_F64 && rows_applicable(gg.wfmt, storage, gg.g, G, 1, ctx->max_smem);
+    for (const Cand &c : candidates(nvec, storage, rows)) {
+        if (c.kernel == TLS_KERNEL_MRHS_ROWS && !rows_applicable(gg.wfmt, storage, gg.g, G, c.vb, ctx->max_smem))
+            continue;
         // one warm-up call, then the timed one
         s = smear_impl(ctx, id, tmp, io, 1, nvec, 1, 0.5, timeslice, storage, c.kernel, c.vb, c.threads, nullptr,
                        nullptr);

@@ -370,3 +370,39 @@ def test_interleaved_groups_bitwise_equal_planar(ctx, T, nvec):
     b, nb = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 12, T.TLS_KERNEL_SINGLE, 4, 0.9, -1)
     assert np.array_equal(a, b)
     assert np.array_equal(na, nb)
+
+
+@pytest.mark.parametrize("dims,nvec,storage", [((8, 8, 8, 3), 5, "F32"), ((16, 8, 8, 2), 24, "F32"),
+                                               ((8, 16, 24, 2), 6, "F16"), ((8, 8, 8, 2), 3, "BF16"),
+                                               ((6, 4, 8, 2), 4, "F32"), ((8, 4, 4, 1), 300, "F32"),
+                                               ((24, 8, 8, 1), 2, "F16")])
+def test_rows_kernel_bitwise_equal_single(ctx, T, dims, nvec, storage):
+    """TMA row-staged multi-RHS kernel == one vector per launch, bitwise (falls back when hx % 4 != 0)."""
+    U = gauge(dims, "haar", 31)
+    vecs = synth.gaussian_vectors(dims, nvec, 32, dtype=torch.complex64)
+    st = getattr(T, "TLS_" + storage)
+    for t0 in (-1, 1 if dims[3] > 1 else 0):
+        a, na = _run(ctx, T, U, dims, vecs, st, T.TLS_F32, 18, T.TLS_KERNEL_MRHS_ROWS, 5, 1.1, t0)
+        b, nb = _run(ctx, T, U, dims, vecs, st, T.TLS_F32, 18, T.TLS_KERNEL_SINGLE, 5, 1.1, t0)
+        assert np.array_equal(a, b)
+        assert np.array_equal(na, nb)
+    if storage == "F32":
+        want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), 5, 1.1)
+        a, _ = _run(ctx, T, U, dims, vecs, st, T.TLS_F32, 18, T.TLS_KERNEL_MRHS_ROWS, 5, 1.1, -1)
+        assert max(per_vector_rel_l2(a, want)) <= 2e-6 * 5
+
+
+def test_rows_kernel_at_headline_shape_sampled(ctx, T):
+    """64^3 slices with 24 vectors (the headline row shape) on 2 slices vs the oracle."""
+    dims = (64, 64, 64, 2)
+    U = gauge_dev(dims, "near", 33, eps=0.2)
+    vecs = synth.gaussian_vectors(dims, 24, 34, dtype=torch.complex64, device="cuda")
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.build_twolink(gid, T.TLS_F32, 18)
+    ref = {v: vecs[v, 1:2].cpu().numpy().astype(np.complex128) for v in (0, 13, 23)}
+    ctx.smear(gid, vecs, T.TLS_F32, 24, 8, 1.6, storage=T.TLS_F32, kernel=T.TLS_KERNEL_MRHS_ROWS)
+    ctx.free_gauge(gid)
+    W = oracle.twolink(U[1:2].cpu().numpy())
+    for v, src in ref.items():
+        want = oracle.smear(W, src, 8, 1.6)
+        assert rel_l2(vecs[v, 1:2].cpu().numpy().astype(np.complex128), want) <= 2e-6 * 8
