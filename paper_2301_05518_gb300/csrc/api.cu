@@ -194,6 +194,22 @@ static Gauge *find_gauge(tls_ctx *ctx, tls_gauge_id id)
 
 static const long long kDefaultBudget = 20000000LL;  // polls of ~64 ns: about a second or more
 
+// Device-usable address of pinned (page-locked) host memory, or nullptr.
+// With unified addressing, memory from cudaHostAlloc / cudaHostRegister can be
+// read and written by kernels directly (over NVLink-C2C on Grace systems), so
+// the layout kernels stream it without a staging copy.  Pageable memory gets
+// nullptr and goes through a staged cudaMemcpy instead.
+static void *pinned_device_ptr(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr) return a.devicePointer;
+    return nullptr;
+}
+
 }  // namespace tls
 
 using namespace tls;
@@ -318,8 +334,9 @@ tls_status tls_load_gauge(tls_ctx *ctx, const double *U, int nd, const int dims[
     cudaError_t e = cudaMemsetAsync(gg.Up, 0, gg.Up_bytes, st);
     const int64_t Vslice = (int64_t)dims[0] * dims[1] * dims[2];
     const size_t slice_bytes = (size_t)Vslice * nd * 144;
-    if (e == cudaSuccess && on_device) {
-        e = launch_ingest_gauge(U, nd, gg.Up, gg.g, gg.L, st);
+    const void *U_dev = on_device ? (const void *)U : pinned_device_ptr(U);
+    if (e == cudaSuccess && U_dev) {
+        e = launch_ingest_gauge((const double *)U_dev, nd, gg.Up, gg.g, gg.L, st);
     } else if (e == cudaSuccess) {
         // Host input: stage a few slices at a time.
         int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(dims[3], (int64_t)(1ULL << 30) / (int64_t)slice_bytes));
@@ -549,6 +566,10 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     const bool il_layout = kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS;
     const int G = il_layout ? std::min(nvec, 256) : nvec;
 
+    // Pinned host vectors are streamed by the layout kernels directly.
+    void *vecs_dev = vecs_on_device ? vecs : pinned_device_ptr(vecs);
+    const bool staged = vecs_dev == nullptr;
+
     // Workspace.
     size_t a_bytes = (size_t)vs * G;
     s = ensure(ctx, ctx->A, a_bytes, "tls_smear: vector buffer A");
@@ -557,7 +578,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     if (s == TLS_OK && norms_out)
         s = ensure(ctx, ctx->partials, sizeof(double) * kNormParts * nvec, "tls_smear: partials");
     if (s == TLS_OK && norms_out) s = ensure(ctx, ctx->norms, sizeof(double) * nvec, "tls_smear: norms");
-    if (s == TLS_OK && !vecs_on_device)
+    if (s == TLS_OK && staged)
         s = ensure(ctx, ctx->staging, io_slice_bytes * nsl * nvec, "tls_smear: host staging");
     if (s != TLS_OK) return s;
     if (ctx->h_alpha_n < (size_t)nvec) {
@@ -628,9 +649,9 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     char *dst_io = nullptr;
     int64_t io_vstride_sites = V;  // sites between vectors in the canonical buffer
     int t_rel = t_first;
-    if (vecs_on_device) {
-        src_io = (const char *)vecs;
-        dst_io = (char *)vecs;
+    if (!staged) {
+        src_io = (const char *)vecs_dev;
+        dst_io = (char *)vecs_dev;
     } else {
         const size_t width_b = io_slice_bytes * nsl;
         const size_t pitch = (size_t)V * 6 * io_elem;
@@ -743,7 +764,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
             e = cudaMemcpyAsync(ctx->h_norms, ctx->norms.p, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st);
     }
     mark(6);
-    if (e == cudaSuccess && !vecs_on_device) {
+    if (e == cudaSuccess && staged) {
         const size_t width_b = io_slice_bytes * nsl;
         const size_t pitch = (size_t)V * 6 * io_elem;
         e = cudaMemcpy2DAsync((char *)vecs + (size_t)t_first * io_slice_bytes, pitch, ctx->staging.p, width_b,

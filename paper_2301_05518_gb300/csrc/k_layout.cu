@@ -300,6 +300,90 @@ __global__ void __launch_bounds__(256) k_norm_partials(const IO *__restrict__ ba
     if (threadIdx.x == 0) partials[(int64_t)v * gridDim.x + blockIdx.x] = red[0];
 }
 
+// Row transposes between the canonical layout and the interleaved records.
+// One CTA per canonical x-row (t, z, y): the row's Lx sites are two x'-rows
+// of hx records groups in sublattices (x even) and (x odd), each a contiguous
+// segment of hx * nvec records.  Both segments go through shared memory so
+// that the global side of either layout is read and written in contiguous
+// runs (nvec canonical rows of Lx sites, two record segments).
+template <typename IO, int VP>
+__global__ void __launch_bounds__(256) k_unpack_rows(const char *__restrict__ src, IO *__restrict__ dst, int64_t dvs,
+                                                     SubGeom g, int Lx, int Ly, int Lz, int t_first, int nvec,
+                                                     int rec_n, int rec_v0)
+{
+    extern __shared__ __align__(16) unsigned char smr[];
+    constexpr int VBY = vfmt_bytes(VP);
+    const int y = blockIdx.x % Ly, z = blockIdx.x / Ly;
+    const int ts = blockIdx.y;
+    const int hx = g.hx;
+    const int sub0 = ((y & 1) << 1) | ((z & 1) << 2);
+    const int r = ((z >> 1) * g.hy + (y >> 1)) * hx;
+    const int segB = hx * rec_n * VBY;
+    // stage both x'-rows (all rec_n records) with 16-byte loads
+    for (int par = 0; par < 2; ++par) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + (((int64_t)(ts * 8 + (sub0 | par)) * g.Ps + r) * rec_n) * VBY);
+        uint4 *d4 = reinterpret_cast<uint4 *>(smr + par * segB);
+        for (int k = threadIdx.x; k < segB / 16; k += blockDim.x) d4[k] = s4[k];
+    }
+    __syncthreads();
+    typedef typename VRec<VP>::R R;
+    const int64_t site0 = (((int64_t)(t_first + ts) * Lz + z) * Ly + y) * Lx;
+    for (int k = threadIdx.x; k < nvec * Lx; k += blockDim.x) {
+        const int v = k / Lx, x = k - v * Lx;
+        cpx<R> val[3];
+        VRec<VP>::load(reinterpret_cast<const char *>(smr) + (x & 1) * segB + ((x >> 1) * rec_n + rec_v0 + v) * VBY, val);
+        IO *p = dst + ((int64_t)v * dvs + site0 + x) * 6;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            p[2 * c] = (IO)val[c].re;
+            p[2 * c + 1] = (IO)val[c].im;
+        }
+    }
+}
+
+template <typename IO, int VP>
+__global__ void __launch_bounds__(256) k_pack_rows(const IO *__restrict__ src, int64_t svs, char *__restrict__ dst,
+                                                   SubGeom g, int Lx, int Ly, int Lz, int t_first, int nvec, int rec_n,
+                                                   int rec_v0)
+{
+    extern __shared__ __align__(16) unsigned char smr[];
+    constexpr int VBY = vfmt_bytes(VP);
+    const int y = blockIdx.x % Ly, z = blockIdx.x / Ly;
+    const int ts = blockIdx.y;
+    const int hx = g.hx;
+    const int sub0 = ((y & 1) << 1) | ((z & 1) << 2);
+    const int r = ((z >> 1) * g.hy + (y >> 1)) * hx;
+    const int segB = hx * rec_n * VBY;
+    const bool partial = nvec != rec_n;
+    if (partial) {  // keep the records of the other slots: start from the current segments
+        for (int par = 0; par < 2; ++par) {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(dst + (((int64_t)(ts * 8 + (sub0 | par)) * g.Ps + r) * rec_n) * VBY);
+            uint4 *d4 = reinterpret_cast<uint4 *>(smr + par * segB);
+            for (int k = threadIdx.x; k < segB / 16; k += blockDim.x) d4[k] = s4[k];
+        }
+        __syncthreads();
+    }
+    typedef typename VRec<VP>::R R;
+    const int64_t site0 = (((int64_t)(t_first + ts) * Lz + z) * Ly + y) * Lx;
+    for (int k = threadIdx.x; k < nvec * Lx; k += blockDim.x) {
+        const int v = k / Lx, x = k - v * Lx;
+        const IO *p = src + ((int64_t)v * svs + site0 + x) * 6;
+        cpx<R> val[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            val[c].re = (R)p[2 * c];
+            val[c].im = (R)p[2 * c + 1];
+        }
+        VRec<VP>::store(reinterpret_cast<char *>(smr) + (x & 1) * segB + ((x >> 1) * rec_n + rec_v0 + v) * VBY, val);
+    }
+    __syncthreads();
+    for (int par = 0; par < 2; ++par) {
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + (((int64_t)(ts * 8 + (sub0 | par)) * g.Ps + r) * rec_n) * VBY);
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(smr + par * segB);
+        for (int k = threadIdx.x; k < segB / 16; k += blockDim.x) d4[k] = s4[k];
+    }
+}
+
 inline int spb_of(int nvec) { return std::max(1, 256 / nvec); }
 
 inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -460,6 +544,38 @@ static cudaError_t unpack_il_io(const char *src, int prec, IO *dst, int64_t dvs,
     return cudaGetLastError();
 }
 
+static bool rows_transpose_ok(const SubGeom &g, int rec_n, int prec, const int L[4])
+{
+    const int segB = g.hx * rec_n * vfmt_bytes(prec);
+    return segB % 16 == 0 && 2 * segB <= 48 * 1024 && (int64_t)L[1] * L[2] <= 0x7fffffff;
+}
+
+template <typename IO>
+static cudaError_t rows_io(bool pack, const void *src, int64_t svs, void *dst, int prec, const SubGeom &g,
+                           const int L[4], int t_first, int nsl, int nvec, int rec_n, int rec_v0, cudaStream_t s)
+{
+    dim3 grid((unsigned)(L[1] * L[2]), nsl);
+    const int smem = 2 * g.hx * rec_n * vfmt_bytes(prec);
+#define TLS_ROWS_CASE(P)                                                                                            \
+    case P:                                                                                                         \
+        if (pack)                                                                                                   \
+            k_pack_rows<IO, P><<<grid, 256, smem, s>>>((const IO *)src, svs, (char *)dst, g, L[0], L[1], L[2],       \
+                                                      t_first, nvec, rec_n, rec_v0);                                \
+        else                                                                                                        \
+            k_unpack_rows<IO, P><<<grid, 256, smem, s>>>((const char *)src, (IO *)dst, svs, g, L[0], L[1], L[2],     \
+                                                        t_first, nvec, rec_n, rec_v0);                              \
+        break;
+    switch (prec) {
+        TLS_ROWS_CASE(P_F64)
+        TLS_ROWS_CASE(P_F32)
+        TLS_ROWS_CASE(P_F16)
+        TLS_ROWS_CASE(P_BF16)
+    default: return cudaErrorNotSupported;
+    }
+#undef TLS_ROWS_CASE
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_il(const void *src, int io_prec, int64_t src_vstride_sites, char *dst, int prec,
                            const SubGeom &g, const int L[4], int t_first, int nsl, int nvec, int rec_n, int rec_v0,
                            cudaStream_t s)
@@ -467,6 +583,12 @@ cudaError_t launch_pack_il(const void *src, int io_prec, int64_t src_vstride_sit
     const int64_t nsite = (int64_t)nsl * 8 * g.Vs;
     if (nsite == 0 || nvec == 0) return cudaSuccess;
     if (nvec > 256 || rec_v0 < 0 || rec_v0 + nvec > rec_n) return cudaErrorInvalidValue;
+    if (rows_transpose_ok(g, rec_n, prec, L)) {
+        if (io_prec == P_F64)
+            return rows_io<double>(true, src, src_vstride_sites, dst, prec, g, L, t_first, nsl, nvec, rec_n, rec_v0, s);
+        if (io_prec == P_F32)
+            return rows_io<float>(true, src, src_vstride_sites, dst, prec, g, L, t_first, nsl, nvec, rec_n, rec_v0, s);
+    }
     if (io_prec == P_F64)
         return pack_il_io<double>((const double *)src, src_vstride_sites, dst, prec, g, L, t_first, nsite, nvec, rec_n,
                                   rec_v0, s);
@@ -483,6 +605,12 @@ cudaError_t launch_unpack_il(const char *src, int prec, void *dst, int io_prec, 
     const int64_t nsite = (int64_t)nsl * 8 * g.Vs;
     if (nsite == 0 || nvec == 0) return cudaSuccess;
     if (nvec > 256 || rec_v0 < 0 || rec_v0 + nvec > rec_n) return cudaErrorInvalidValue;
+    if (rows_transpose_ok(g, rec_n, prec, L)) {
+        if (io_prec == P_F64)
+            return rows_io<double>(false, src, dst_vstride_sites, dst, prec, g, L, t_first, nsl, nvec, rec_n, rec_v0, s);
+        if (io_prec == P_F32)
+            return rows_io<float>(false, src, dst_vstride_sites, dst, prec, g, L, t_first, nsl, nvec, rec_n, rec_v0, s);
+    }
     if (io_prec == P_F64)
         return unpack_il_io<double>(src, prec, (double *)dst, dst_vstride_sites, g, L, t_first, nsite, nvec, rec_n,
                                     rec_v0, s);

@@ -39,6 +39,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
 {
     unsigned ok;
@@ -77,7 +82,7 @@ inline RowsPlan rows_plan(int hx, int nvec, int vby, int wb)
     RowsPlan p{};
     p.rowB = hx * nvec * vby;
     p.wrowB = hx * wb;
-    p.offY = 128;                             // 2 mbarriers at 0
+    p.offY = 128;                             // 4 mbarriers at 0 (full[2], empty[2])
     p.offZ = p.offY + 4 * up(p.rowB);         // Y ring of 4
     p.offW = p.offZ + 4 * up(p.rowB);         // Z [parity][minus, plus]
     p.offWz = p.offW + 9 * up(p.wrowB);       // Wc [ring 3][dir 3]
@@ -91,8 +96,14 @@ template <int WF> struct WPlanes {
     static constexpr int REM = WB % 16;
 };
 
+// Shared memory allows one or two CTAs per SM, so the launch bound scales
+// with VB and leaves the compiler registers to hoist the next loads.
+template <int VB> struct RowsBound {
+    static constexpr int threads = VB == 1 ? 768 : VB == 2 ? 384 : 256;
+};
+
 template <int VP, int WF, int VB, bool A16>
-__global__ void __launch_bounds__(768) k_step_rows(const char *__restrict__ W, const char *__restrict__ in,
+__global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char *__restrict__ W, const char *__restrict__ in,
                                                    char *__restrict__ out, const double *__restrict__ alpha,
                                                    SubGeom g, int nvec, RowsPlan pl, int *err)
 {
@@ -131,6 +142,9 @@ __global__ void __launch_bounds__(768) k_step_rows(const char *__restrict__ W, c
     const int vg = tid - xq * tx;
     const int v0 = vg * VB;
     const bool worker = xq < hx;
+    R a_v[VB];  // alpha per vector, converted once (keeps FP64 out of the row loop)
+#pragma unroll
+    for (int k = 0; k < VB; ++k) a_v[k] = worker ? (R)alpha[v0 + k] : R(0);
 
     auto row_of = [&](int z, int y) { return (z * hy + y) * hx; };
     auto ring4 = [](int r) { return (r + 4) & 3; };
@@ -161,18 +175,24 @@ __global__ void __launch_bounds__(768) k_step_rows(const char *__restrict__ W, c
         load_wrow(Wz + (r & 1) * wS, 2, row_of(zm, y), bar);
     };
 
+    // full[b]: the stage of parity b has landed (1 arrival + transaction bytes).
+    // empty[b]: every warp has finished the row of parity b (one arrival per warp).
+    uint64_t *full = bars, *empty = bars + 2;
+    const int nwarps = (blockDim.x + 31) / 32;
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], nwarps);
+        mbar_init(&empty[1], nwarps);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    // Prologue on barrier 1 (its first phase): psi rows -1 and 0, W rows -1.
-    // Then stage 0 on barrier 0.
-    unsigned ph0 = 0u, ph1 = 0u;
+    // Prologue on full[1] (its first phase): psi rows -1 and 0, W rows -1.
+    // Then stage 0 on full[0].
+    unsigned fph0 = 0u, fph1 = 0u;
     if (tid == 0) {
-        uint64_t *bar = &bars[1];
+        uint64_t *bar = &full[1];
         mbar_expect_tx(bar, 2 * row_bytes + 3 * wrow_bytes);
         bulk_load(Y + ring4(-1) * rowS, inblk + (int64_t)row_of(zq, hy - 1) * recB, row_bytes, bar);
         bulk_load(Y + ring4(0) * rowS, inblk + (int64_t)row_of(zq, 0) * recB, row_bytes, bar);
@@ -181,25 +201,32 @@ __global__ void __launch_bounds__(768) k_step_rows(const char *__restrict__ W, c
         issue_stage(0);
     }
     const long long kLimit = 1LL << 22;
-    auto wait_bar = [&](int b) -> bool {
-        unsigned &ph = b ? ph1 : ph0;
+    auto wait_on = [&](uint64_t *bar, unsigned parity) -> bool {
         long long n = 0;
-        while (!mbar_try_wait(&bars[b], ph)) {
+        while (!mbar_try_wait(bar, parity)) {
             if (++n > kLimit) return false;
         }
+        return true;
+    };
+    auto wait_full = [&](int b) -> bool {
+        unsigned &ph = b ? fph1 : fph0;
+        if (!wait_on(&full[b], ph)) return false;
         ph ^= 1u;
         return true;
     };
-    bool ok = wait_bar(1);
+    bool ok = wait_full(1);
 
     for (int y = 0; y < hy && ok; ++y) {
-        // Stage y+1 goes out before row y is computed.  Its slots were last
-        // read by row y-1, which every thread finished (barrier at loop end).
+        // Stage y+1 refills the slots row y-1 read: the producer waits until
+        // every warp has released row y-1, the other warps run on.
         if (tid == 0 && y + 1 < hy) {
-            fence_proxy_async_smem();
-            issue_stage(y + 1);
+            if (y >= 1) ok = wait_on(&empty[(y - 1) & 1], ((y - 1) >> 1) & 1);
+            if (ok) {
+                fence_proxy_async_smem();
+                issue_stage(y + 1);
+            }
         }
-        ok = wait_bar(y & 1);
+        if (ok) ok = wait_full(y & 1);
         if (!ok) break;
         if (worker) {
             const int xp = xq == hx - 1 ? 0 : xq + 1;
@@ -211,44 +238,40 @@ __global__ void __launch_bounds__(768) k_step_rows(const char *__restrict__ W, c
             const char *Wzm = Wz + (y & 1) * wS;
             const unsigned rs = (unsigned)recB;
             const unsigned vo = (unsigned)v0 * VBY;
+            // Operand addresses of the six hops, in the order of site_step:
+            // x forward, x backward, y forward, y backward, z forward, z backward.
+            const char *wsrc[6] = {Wrow, Wrow, Wrow + wS, Wym, Wrow + 2 * wS, Wzm};
+            const int wsite[6] = {xq, xm, xq, xq, xq, xq};
+            const char *psrc[6] = {Yc + xp * rs + vo, Yc + xm * rs + vo, Yp + xq * rs + vo,
+                                   Ym + xq * rs + vo, Zp + xq * rs + vo, Zm + xq * rs + vo};
             cpx<R> acc[VB][3];
 #pragma unroll
             for (int k = 0; k < VB; ++k)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) acc[k][c].re = acc[k][c].im = R(0);
-            cpx<R> m[9], p[VB][3];
-            // x: forward W_x(x) psi(x+2x), backward W_x(x-2x)^dag psi(x-2x)
-            WFmt<WF>::load(Wrow + 0 * wS, hx, xq, m);
-            RecGroup<VP, VB, A16>::load(Yc + xp * rs + vo, p);
+            // software pipeline: the operands of hop h+1 are loaded before hop h is applied
+            cpx<R> m[2][9], p[2][VB][3];
+            WFmt<WF>::load(wsrc[0], hx, wsite[0], m[0]);
+            RecGroup<VP, VB, A16>::load(psrc[0], p[0]);
 #pragma unroll
-            for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
-            WFmt<WF>::load(Wrow + 0 * wS, hx, xm, m);
-            RecGroup<VP, VB, A16>::load(Yc + xm * rs + vo, p);
+            for (int h = 0; h < 6; ++h) {
+                if (h + 1 < 6) {
+                    WFmt<WF>::load(wsrc[h + 1], hx, wsite[h + 1], m[(h + 1) & 1]);
+                    RecGroup<VP, VB, A16>::load(psrc[h + 1], p[(h + 1) & 1]);
+                }
 #pragma unroll
-            for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
-            // y
-            WFmt<WF>::load(Wrow + 1 * wS, hx, xq, m);
-            RecGroup<VP, VB, A16>::load(Yp + xq * rs + vo, p);
-#pragma unroll
-            for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
-            WFmt<WF>::load(Wym, hx, xq, m);
-            RecGroup<VP, VB, A16>::load(Ym + xq * rs + vo, p);
-#pragma unroll
-            for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
-            // z
-            WFmt<WF>::load(Wrow + 2 * wS, hx, xq, m);
-            RecGroup<VP, VB, A16>::load(Zp + xq * rs + vo, p);
-#pragma unroll
-            for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
-            WFmt<WF>::load(Wzm, hx, xq, m);
-            RecGroup<VP, VB, A16>::load(Zm + xq * rs + vo, p);
-#pragma unroll
-            for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
+                for (int k = 0; k < VB; ++k) {
+                    if (h & 1)
+                        mdv_add(m[h & 1], p[h & 1][k], acc[k]);
+                    else
+                        mv_add(m[h & 1], p[h & 1][k], acc[k]);
+                }
+            }
             cpx<R> c[VB][3], o[VB][3];
             RecGroup<VP, VB, A16>::load(Yc + xq * rs + vo, c);
 #pragma unroll
             for (int k = 0; k < VB; ++k) {
-                const R a = (R)alpha[v0 + k];
+                const R a = a_v[k];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     o[k][q].re = fma(a, fma(R(-6), c[k][q].re, acc[k][q].re), c[k][q].re);
@@ -256,17 +279,18 @@ __global__ void __launch_bounds__(768) k_step_rows(const char *__restrict__ W, c
                 }
             }
             RecGroup<VP, VB, A16>::store(outblk + ((int64_t)row_of(zq, y) + xq) * recB + vo, o);
-        }
-        __syncthreads();
+                }
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[y & 1]);
     }
     if (!ok) {
         atomicOr(err, DERR_TIMEOUT);
         // let this CTA's own copies land before shared memory goes away
         long long n = 0;
-        while (!mbar_try_wait(&bars[0], ph0) && ++n < kLimit) {
+        while (!mbar_try_wait(&full[0], fph0) && ++n < kLimit) {
         }
         n = 0;
-        while (!mbar_try_wait(&bars[1], ph1) && ++n < kLimit) {
+        while (!mbar_try_wait(&full[1], fph1) && ++n < kLimit) {
         }
     }
 }
@@ -278,7 +302,8 @@ inline bool rows_ok(int wfmt, int prec, const SubGeom &g, int nvec, int vb, int 
     if (g.hx % 4 != 0) return false;  // 16-byte bulk copies of every plane segment
     if (vb < 1 || nvec % vb != 0) return false;
     const int threads = g.hx * (nvec / vb);
-    if (threads > 768 || threads < 32) return false;
+    const int bound = vb == 1 ? 768 : vb == 2 ? 384 : 256;
+    if (threads > bound || threads < 32) return false;
     if ((g.hx * nvec * vby) % 16 != 0) return false;
     (void)wb;
     RowsPlan p = rows_plan(g.hx, nvec, vby, wb);

@@ -64,10 +64,10 @@ def gauge(dims, kind, seed, eps=0.3, nd=4):
 
 # ------------------------------------------------------------------ ingest
 @pytest.mark.parametrize("dims", [(4, 6, 8, 3), (2, 2, 2, 1), (6, 10, 4, 2), (8, 8, 8, 2)])
-@pytest.mark.parametrize("nd,on_device", [(4, False), (3, True)])
+@pytest.mark.parametrize("nd,on_device", [(4, False), (3, True), (4, "pinned")])
 def test_ingest_roundtrip_bit_exact(ctx, T, dims, nd, on_device):
     U = gauge(dims, "haar", 5, nd=nd)
-    src = U.cuda() if on_device else U
+    src = U.pin_memory() if on_device == "pinned" else (U.cuda() if on_device else U)
     gid = ctx.load_gauge(src, nd, dims)
     out = np.zeros(U.shape[:4] + (3, 3, 3), dtype=np.complex128)
     ctx.export_gauge(gid, out)
@@ -110,7 +110,7 @@ def _run(ctx, T, U, dims, vecs, storage, wprec, recon, kernel, N, sigma, t0, io=
     io = io if io is not None else (T.TLS_F64 if storage == T.TLS_F64 else T.TLS_F32)
     dt = torch.complex128 if io == T.TLS_F64 else torch.complex64
     x = vecs.to(dt).contiguous()
-    x = x if host else x.cuda()
+    x = (x.pin_memory() if host == "pinned" else x) if host else x.cuda()
     norms = ctx.smear(gid, x, io, x.shape[0], N, sigma, timeslice=t0, storage=storage, kernel=kernel,
                       norms=True)
     ctx.free_gauge(gid)
@@ -200,15 +200,20 @@ def test_zero_steps_and_zero_width_are_identity(ctx, T, storage):
         assert np.array_equal(got, ref)
 
 
-def test_host_buffers_match_device(ctx, T):
-    dims = (6, 6, 4, 3)
+@pytest.mark.parametrize("kern", ["MRHS", "SINGLE", "MRHS_ROWS"])
+def test_host_buffers_match_device(ctx, T, kern):
+    """Pageable host vectors (staged copies) and pinned ones (read by the kernels over C2C)."""
+    dims = (8, 6, 4, 3)
     U = gauge(dims, "near", 19)
     vecs = synth.gaussian_vectors(dims, 3, 20)
+    k = getattr(T, "TLS_KERNEL_" + kern)
     for t0 in (-1, 2):
-        dev, _ = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 18, T.TLS_KERNEL_MRHS, 5, 1.0, t0)
-        host, _ = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 18, T.TLS_KERNEL_MRHS, 5, 1.0, t0,
-                       host=True)
+        dev, nd = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 18, k, 5, 1.0, t0)
+        host, nh = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 18, k, 5, 1.0, t0, host=True)
+        pinned, npn = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 18, k, 5, 1.0, t0, host="pinned")
         assert np.array_equal(dev, host)
+        assert np.array_equal(dev, pinned)
+        assert np.array_equal(nd, nh) and np.array_equal(nd, npn)
 
 
 def test_two_site_extent(ctx, T):
