@@ -566,8 +566,13 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     const bool il_layout = kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS;
     const int G = il_layout ? std::min(nvec, 256) : nvec;
 
-    // Pinned host vectors are streamed by the layout kernels directly.
-    void *vecs_dev = vecs_on_device ? vecs : pinned_device_ptr(vecs);
+    // Pinned host vectors are streamed by the layout kernels directly when
+    // those read and write whole canonical rows (the interleaved row
+    // transposes); other layouts go through staged bulk copies.
+    const bool il_rows = (kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS) &&
+                         rows_transpose_ok(g, std::min(nvec, 256), storage, gg->L) &&
+                         (nvec <= 256 || rows_transpose_ok(g, nvec % 256 ? nvec % 256 : 256, storage, gg->L));
+    void *vecs_dev = vecs_on_device ? vecs : (il_rows ? pinned_device_ptr(vecs) : nullptr);
     const bool staged = vecs_dev == nullptr;
 
     // Workspace.

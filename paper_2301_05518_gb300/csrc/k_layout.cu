@@ -37,22 +37,28 @@ __device__ __forceinline__ Coords coords_of(const SubGeom &g, int sub, int i)
     return c;
 }
 
+// Thread per (canonical site, direction, complex entry), entry fastest: a warp
+// reads 512 contiguous bytes of the canonical links (host memory over C2C
+// included) and scatters them into the 9 planes of each (block, direction).
 __global__ void k_ingest_gauge(const double *__restrict__ U, int nd, double2 *__restrict__ Up, SubGeom g, int Lx,
                                int Ly, int Lz, int64_t total)
 {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
-    const int i = (int)(idx % g.Vs);
-    const int64_t r = idx / g.Vs;
-    const int d = (int)(r % 3);
-    const int b = (int)(r / 3);
-    const int t = b >> 3, sub = b & 7;
-    Coords c = coords_of(g, sub, i);
-    const int64_t site = (((int64_t)t * Lz + c.z) * Ly + c.y) * Lx + c.x;
-    const double2 *src = reinterpret_cast<const double2 *>(U) + (site * nd + d) * 9;
-    double2 *dst = Up + ((int64_t)b * 3 + d) * 9 * g.Ps + i;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) dst[k * g.Ps] = src[k];
+    const int k = (int)(idx % 27);
+    const int64_t site = idx / 27;
+    const int d = k / 9, e = k - d * 9;
+    const int x = (int)(site % Lx);
+    const int64_t r1 = site / Lx;
+    const int y = (int)(r1 % Ly);
+    const int64_t r2 = r1 / Ly;
+    const int z = (int)(r2 % Lz);
+    const int t = (int)(r2 / Lz);
+    const int sub = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+    const int i = ((z >> 1) * g.hy + (y >> 1)) * g.hx + (x >> 1);
+    const int b = t * 8 + sub;
+    const double2 v = reinterpret_cast<const double2 *>(U)[(site * nd + d) * 9 + e];
+    Up[(((int64_t)b * 3 + d) * 9 + e) * g.Ps + i] = v;
 }
 
 __global__ void k_export_gauge(const double2 *__restrict__ Up, double *__restrict__ out, SubGeom g, int Lx, int Ly,
@@ -422,7 +428,7 @@ cudaError_t unpack_io(const char *src, int prec, int64_t svs, IO *dst, int64_t d
 
 cudaError_t launch_ingest_gauge(const double *U, int nd, double *Up, const SubGeom &g, const int L[4], cudaStream_t s)
 {
-    const int64_t total = (int64_t)L[3] * 8 * 3 * g.Vs;
+    const int64_t total = (int64_t)L[0] * L[1] * L[2] * L[3] * 27;
     if (total == 0) return cudaSuccess;
     k_ingest_gauge<<<nblocks(total, 256), 256, 0, s>>>(U, nd, reinterpret_cast<double2 *>(Up), g, L[0], L[1], L[2],
                                                        total);
@@ -544,7 +550,7 @@ static cudaError_t unpack_il_io(const char *src, int prec, IO *dst, int64_t dvs,
     return cudaGetLastError();
 }
 
-static bool rows_transpose_ok(const SubGeom &g, int rec_n, int prec, const int L[4])
+bool rows_transpose_ok(const SubGeom &g, int rec_n, int prec, const int L[4])
 {
     const int segB = g.hx * rec_n * vfmt_bytes(prec);
     return segB % 16 == 0 && 2 * segB <= 48 * 1024 && (int64_t)L[1] * L[2] <= 0x7fffffff;

@@ -185,17 +185,26 @@ __global__ void __launch_bounds__(256) k_step_il(const char *__restrict__ W, con
     for (int k = 0; k < VB; ++k)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[k][c].re = acc[k][c].im = R(0);
+    // hops in the order of site_step; the operands of hop h+1 are loaded
+    // before hop h is applied
+    cpx<R> m[2][9], p[2][VB][3];
+    WFmt<WF>::load(wb, g.Ps, i, m[0]);
+    RecGroup<VP, VB, A16>::load(rin + (unsigned)fw[0] * rstride, p[0]);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        cpx<R> m[9], p[VB][3];
-        WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, i, m);
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)fw[d] * rstride, p);
+    for (int h = 0; h < 6; ++h) {
+        if (h + 1 < 6) {
+            const int d1 = (h + 1) >> 1;
+            const int s1 = ((h + 1) & 1) ? bw[d1] : fw[d1];
+            WFmt<WF>::load(wb + d1 * g.Ps * WB, g.Ps, ((h + 1) & 1) ? bw[d1] : i, m[(h + 1) & 1]);
+            RecGroup<VP, VB, A16>::load(rin + (unsigned)s1 * rstride, p[(h + 1) & 1]);
+        }
 #pragma unroll
-        for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
-        WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, bw[d], m);
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)bw[d] * rstride, p);
-#pragma unroll
-        for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
+        for (int k = 0; k < VB; ++k) {
+            if (h & 1)
+                mdv_add(m[h & 1], p[h & 1][k], acc[k]);
+            else
+                mv_add(m[h & 1], p[h & 1][k], acc[k]);
+        }
     }
     cpx<R> c[VB][3], o[VB][3];
     RecGroup<VP, VB, A16>::load(rin + (unsigned)i * rstride, c);

@@ -91,6 +91,8 @@ cudaError_t launch_build_twolink(const double *Up, char *W, int wfmt, const SubG
                                  cudaStream_t s);
 cudaError_t launch_export_twolink(const char *W, int wfmt, double *out, const SubGeom &g, const int L[4],
                                   cudaStream_t s);
+// Whether the interleaved pack/unpack use the row transposes (contiguous canonical rows).
+bool rows_transpose_ok(const SubGeom &g, int rec_n, int prec, const int L[4]);
 // Interleaved layout: rec_n <= 256 records per site, record (block, i, r).  Caller vector v
 // (0 <= v < nvec) goes to / comes from record rec_v0 + v.
 cudaError_t launch_pack_il(const void *src, int io_prec, int64_t src_vstride_sites, char *dst, int prec,
