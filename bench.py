@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
-    ap.add_argument("--kernel", default="auto", choices=["auto", "single", "mrhs", "persistent", "rows"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "single", "mrhs", "persistent", "rows", "zm"])
     ap.add_argument("--small", action="store_true", help="16^3x8 lattice, for quick checks only")
     ap.add_argument("--lattice", default=None, help="Lx,Ly,Lz,Lt override (profiling cases)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (planner default)")
@@ -347,7 +347,8 @@ def our_arm(args):
     storage = {"f32": T.TLS_F32, "f16": T.TLS_F16, "bf16": T.TLS_BF16}[args.storage]
     wprec = T.TLS_F32
     kernel = {"auto": T.TLS_KERNEL_AUTO, "single": T.TLS_KERNEL_SINGLE, "mrhs": T.TLS_KERNEL_MRHS,
-              "persistent": T.TLS_KERNEL_PERSISTENT, "rows": T.TLS_KERNEL_MRHS_ROWS}[args.kernel]
+              "persistent": T.TLS_KERNEL_PERSISTENT, "rows": T.TLS_KERNEL_MRHS_ROWS,
+              "zm": T.TLS_KERNEL_MRHS_ZM}[args.kernel]
     N, sigma, nvec = w["N"], w["sigma"], w["nvec"]
     hbm_peak, peak_kind = load_peaks()
 
@@ -365,7 +366,7 @@ def our_arm(args):
         ctx.build_twolink(gid, wprec, T.TLS_R18, keep_U=0, stream=stream)
         best, cands = ctx.autotune(gid, nvec, storage, T.TLS_ALL_T, steps=4)
         ctx.free_gauge(gid)
-        names = {1: "single", 2: "mrhs", 3: "persistent", 4: "mrhs_rows"}
+        names = {1: "single", 2: "mrhs", 3: "persistent", 4: "mrhs_rows", 5: "mrhs_zm"}
         tune = {"best": dict(best, kernel=names[best["kernel"]]),
                 "candidates": [dict(c, kernel=names[c["kernel"]]) for c in cands]}
 
@@ -414,11 +415,11 @@ def our_arm(args):
     per_launch_ms = mean_iter_ms / max(1, iter_launches)
     per_launch_bytes = prof_last["iter_bytes"] / max(1, iter_launches)
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
-    kern_name = {1: "single", 2: "mrhs", 3: "persistent", 4: "mrhs_rows"}.get(prof_last["kernel"], "?")
+    kern_name = {1: "single", 2: "mrhs", 3: "persistent", 4: "mrhs_rows", 5: "mrhs_zm"}.get(prof_last["kernel"], "?")
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": None,
             "kernel": {"persistent": "k_persist", "mrhs": "k_step_il", "mrhs_rows": "k_step_rows",
-                       "single": "k_step"}.get(kern_name, "?"),
+                       "mrhs_zm": "k_step_zm", "single": "k_step"}.get(kern_name, "?"),
             "peak_source": peak_kind,
             "note": ("algorithmic bytes = W once + psi read once + psi written once per site and "
                      "step; persistent launches count all N steps (effective GB/s)")}

@@ -78,6 +78,8 @@ typedef int tls_status;
 #define TLS_KERNEL_MRHS_ROWS  4  /* multi-RHS, rows staged in shared memory by */
                                  /* TMA bulk copies (falls back to MRHS when   */
                                  /* the shape does not allow 16-byte copies)   */
+#define TLS_KERNEL_MRHS_ZM    5  /* multi-RHS, each thread marches along z     */
+                                 /* with the z-neighbours in registers         */
 
 #define TLS_ALL_T (-1)           /* timeslice argument: smear every slice      */
 

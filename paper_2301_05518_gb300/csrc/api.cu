@@ -144,6 +144,17 @@ cudaError_t launch_step_il(const StepArgs &a)
     }
 }
 
+cudaError_t launch_step_zm(const StepArgs &a)
+{
+    switch (a.prec_in) {
+    case P_F64: return launch_step_zm_f64(a);
+    case P_F32: return launch_step_zm_f32(a);
+    case P_F16: return launch_step_zm_f16(a);
+    case P_BF16: return launch_step_zm_bf16(a);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 cudaError_t launch_step_rows(const StepArgs &a, int *err)
 {
     switch (a.prec_in) {
@@ -193,22 +204,6 @@ static Gauge *find_gauge(tls_ctx *ctx, tls_gauge_id id)
 }
 
 static const long long kDefaultBudget = 20000000LL;  // polls of ~64 ns: about a second or more
-
-// Device-usable address of pinned (page-locked) host memory, or nullptr.
-// With unified addressing, memory from cudaHostAlloc / cudaHostRegister can be
-// read and written by kernels directly (over NVLink-C2C on Grace systems), so
-// the layout kernels stream it without a staging copy.  Pageable memory gets
-// nullptr and goes through a staged cudaMemcpy instead.
-static void *pinned_device_ptr(const void *p)
-{
-    cudaPointerAttributes a{};
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr) return a.devicePointer;
-    return nullptr;
-}
 
 }  // namespace tls
 
@@ -334,7 +329,7 @@ tls_status tls_load_gauge(tls_ctx *ctx, const double *U, int nd, const int dims[
     cudaError_t e = cudaMemsetAsync(gg.Up, 0, gg.Up_bytes, st);
     const int64_t Vslice = (int64_t)dims[0] * dims[1] * dims[2];
     const size_t slice_bytes = (size_t)Vslice * nd * 144;
-    const void *U_dev = on_device ? (const void *)U : pinned_device_ptr(U);
+    const void *U_dev = on_device ? (const void *)U : nullptr;
     if (e == cudaSuccess && U_dev) {
         e = launch_ingest_gauge((const double *)U_dev, nd, gg.Up, gg.g, gg.L, st);
     } else if (e == cudaSuccess) {
@@ -503,7 +498,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     if (nvec < 1 || nvec > 65535) return fail(TLS_ERR_ARG, "tls_smear: nvec = %d", nvec);
     if (N < 0) return fail(TLS_ERR_ARG, "tls_smear: N = %d < 0", N);
     if (!std::isfinite(width)) return fail(TLS_ERR_ARG, "tls_smear: width is not finite");
-    if (kernel < TLS_KERNEL_AUTO || kernel > TLS_KERNEL_MRHS_ROWS)
+    if (kernel < TLS_KERNEL_AUTO || kernel > TLS_KERNEL_MRHS_ZM)
         return fail(TLS_ERR_ARG, "tls_smear: kernel %d", kernel);
     std::lock_guard<FairMutex> lk(ctx->mu);
     Gauge *gg = find_gauge(ctx, id);
@@ -549,7 +544,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     if (kern == TLS_KERNEL_SINGLE) {
         vb = 1;
         if (threads <= 0) threads = 128;
-    } else if (kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS) {
+    } else if (kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS || kern == TLS_KERNEL_MRHS_ZM) {
         if (vb <= 0 || vb > 4 || G0 % vb != 0 || (storage == TLS_F64 && vb > 2)) vb = default_il_vb(storage, G0);
         if (threads <= 0) threads = 256;
         // TMA row staging needs 16-byte copies and a row that fits in shared memory
@@ -563,16 +558,14 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         if (threads <= 0) threads = 256;
     }
     // The multi-RHS kernel works on the interleaved layout in groups of <= 256 vectors.
-    const bool il_layout = kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS;
+    const bool il_layout = kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS || kern == TLS_KERNEL_MRHS_ZM;
     const int G = il_layout ? std::min(nvec, 256) : nvec;
 
-    // Pinned host vectors are streamed by the layout kernels directly when
-    // those read and write whole canonical rows (the interleaved row
-    // transposes); other layouts go through staged bulk copies.
-    const bool il_rows = (kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS) &&
-                         rows_transpose_ok(g, std::min(nvec, 256), storage, gg->L) &&
-                         (nvec <= 256 || rows_transpose_ok(g, nvec % 256 ? nvec % 256 : 256, storage, gg->L));
-    void *vecs_dev = vecs_on_device ? vecs : (il_rows ? pinned_device_ptr(vecs) : nullptr);
+    // Host vectors go through bulk copies (DMA) into a staging buffer.  On a
+    // GB300 these measured faster than letting the layout kernels read and
+    // write pinned host memory over NVLink-C2C directly (1236 ms against
+    // 1436-1450 ms for the 64^3x96 step), so zero-copy is not used.
+    void *vecs_dev = vecs_on_device ? vecs : nullptr;
     const bool staged = vecs_dev == nullptr;
 
     // Workspace.
@@ -734,6 +727,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
                         sa.out = (it & 1) ? x : y;
                         sa.alpha = alpha_g + gi;
                         e = kern == TLS_KERNEL_MRHS_ROWS ? launch_step_rows(sa, ctx->d_err)
+                            : kern == TLS_KERNEL_MRHS_ZM ? launch_step_zm(sa)
                             : il                         ? launch_step_il(sa)
                                                          : launch_step(sa);
                         ++launches;

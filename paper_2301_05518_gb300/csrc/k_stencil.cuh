@@ -185,26 +185,17 @@ __global__ void __launch_bounds__(256) k_step_il(const char *__restrict__ W, con
     for (int k = 0; k < VB; ++k)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[k][c].re = acc[k][c].im = R(0);
-    // hops in the order of site_step; the operands of hop h+1 are loaded
-    // before hop h is applied
-    cpx<R> m[2][9], p[2][VB][3];
-    WFmt<WF>::load(wb, g.Ps, i, m[0]);
-    RecGroup<VP, VB, A16>::load(rin + (unsigned)fw[0] * rstride, p[0]);
 #pragma unroll
-    for (int h = 0; h < 6; ++h) {
-        if (h + 1 < 6) {
-            const int d1 = (h + 1) >> 1;
-            const int s1 = ((h + 1) & 1) ? bw[d1] : fw[d1];
-            WFmt<WF>::load(wb + d1 * g.Ps * WB, g.Ps, ((h + 1) & 1) ? bw[d1] : i, m[(h + 1) & 1]);
-            RecGroup<VP, VB, A16>::load(rin + (unsigned)s1 * rstride, p[(h + 1) & 1]);
-        }
+    for (int d = 0; d < 3; ++d) {
+        cpx<R> m[9], p[VB][3];
+        WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, i, m);
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)fw[d] * rstride, p);
 #pragma unroll
-        for (int k = 0; k < VB; ++k) {
-            if (h & 1)
-                mdv_add(m[h & 1], p[h & 1][k], acc[k]);
-            else
-                mv_add(m[h & 1], p[h & 1][k], acc[k]);
-        }
+        for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
+        WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, bw[d], m);
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)bw[d] * rstride, p);
+#pragma unroll
+        for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
     }
     cpx<R> c[VB][3], o[VB][3];
     RecGroup<VP, VB, A16>::load(rin + (unsigned)i * rstride, c);
@@ -232,6 +223,108 @@ __global__ void __launch_bounds__(256) k_step_il(const char *__restrict__ W, con
 #pragma unroll
         for (int k = 0; k < VB; ++k)
             if (on[k]) VRec<VP>::store(rout + (unsigned)i * rstride + k * VBY, o[k]);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Multi-RHS step on the interleaved layout, marching along z'.
+// CTA = (nvec/VB, spb): threadIdx.x picks VB adjacent vectors, threadIdx.y
+// one of spb consecutive x' of row y' = blockIdx.y in block blockIdx.z; each
+// thread then walks its column z' = 0 .. hz-1.  psi(z-1), psi(z), psi(z+1)
+// and W_z(z-1) stay in registers from one site to the next, so per site only
+// psi(z+2)'s prefetch, the x and y neighbours and five W matrices are loaded.
+// Same per-vector FMA sequence as site_step (bitwise equal results).
+// --------------------------------------------------------------------------
+template <int VP, int WF, int VB, bool A16>
+__global__ void __launch_bounds__(256) k_step_zm(const char *__restrict__ W, const char *__restrict__ in,
+                                                 char *__restrict__ out, const double *__restrict__ alpha,
+                                                 SubGeom g, int nvec)
+{
+    typedef typename VRec<VP>::R R;
+    constexpr int WB = wfmt_bytes(WF);
+    constexpr int VBY = vfmt_bytes(VP);
+    const int v0 = threadIdx.x * VB;
+    const int xq = blockIdx.x * blockDim.y + threadIdx.y;
+    if (xq >= g.hx) return;
+    const int yq = blockIdx.y;
+    const int blk = blockIdx.z;
+    const int sy = g.hx, sz = g.hx * g.hy, hz = g.hz;
+    const int xp = xq == g.hx - 1 ? xq - (g.hx - 1) : xq + 1;
+    const int xm = xq == 0 ? xq + (g.hx - 1) : xq - 1;
+    const int yp = yq == g.hy - 1 ? 0 : yq + 1;
+    const int ym = yq == 0 ? g.hy - 1 : yq - 1;
+    const char *wb = W + (int64_t)blk * 3 * g.Ps * WB;
+    const char *rin = in + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
+    char *rout = out + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
+    const unsigned rstride = (unsigned)nvec * VBY;
+    R a_v[VB];
+#pragma unroll
+    for (int k = 0; k < VB; ++k) a_v[k] = (R)alpha[v0 + k];
+    const int col = yq * sy + xq;       // site index at z' = 0
+    auto site = [&](int z) { return z * sz + col; };
+    // column state: psi(z-1), psi(z), psi(z+1) and W_z(z-1)
+    cpx<R> pm[VB][3], pc[VB][3], pp[VB][3], wzm[9];
+    RecGroup<VP, VB, A16>::load(rin + (unsigned)site(hz - 1) * rstride, pm);
+    RecGroup<VP, VB, A16>::load(rin + (unsigned)site(0) * rstride, pc);
+    RecGroup<VP, VB, A16>::load(rin + (unsigned)site(1 % hz) * rstride, pp);
+    WFmt<WF>::load(wb + 2 * g.Ps * WB, g.Ps, site(hz - 1), wzm);
+    for (int z = 0; z < hz; ++z) {
+        const int i = site(z);
+        const int zn = (z + 2) % hz;
+        cpx<R> pn[VB][3];  // psi(z+2): next iteration's psi(z+1)
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)site(zn) * rstride, pn);
+        cpx<R> acc[VB][3];
+#pragma unroll
+        for (int k = 0; k < VB; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[k][c].re = acc[k][c].im = R(0);
+        cpx<R> m[9], p[VB][3], wz[9];
+        // x forward / backward
+        WFmt<WF>::load(wb, g.Ps, i, m);
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)(i - xq + xp) * rstride, p);
+#pragma unroll
+        for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
+        WFmt<WF>::load(wb, g.Ps, i - xq + xm, m);
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)(i - xq + xm) * rstride, p);
+#pragma unroll
+        for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
+        // y forward / backward
+        WFmt<WF>::load(wb + g.Ps * WB, g.Ps, i, m);
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)(i + (yp - yq) * sy) * rstride, p);
+#pragma unroll
+        for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
+        WFmt<WF>::load(wb + g.Ps * WB, g.Ps, i + (ym - yq) * sy, m);
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)(i + (ym - yq) * sy) * rstride, p);
+#pragma unroll
+        for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
+        // z forward (W_z(z), psi(z+1)) / backward (W_z(z-1), psi(z-1)), from registers
+        WFmt<WF>::load(wb + 2 * g.Ps * WB, g.Ps, i, wz);
+#pragma unroll
+        for (int k = 0; k < VB; ++k) mv_add(wz, pp[k], acc[k]);
+#pragma unroll
+        for (int k = 0; k < VB; ++k) mdv_add(wzm, pm[k], acc[k]);
+        cpx<R> o[VB][3];
+#pragma unroll
+        for (int k = 0; k < VB; ++k) {
+            const R a = a_v[k];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                o[k][q].re = fma(a, fma(R(-6), pc[k][q].re, acc[k][q].re), pc[k][q].re);
+                o[k][q].im = fma(a, fma(R(-6), pc[k][q].im, acc[k][q].im), pc[k][q].im);
+            }
+        }
+        RecGroup<VP, VB, A16>::store(rout + (unsigned)i * rstride, o);
+        // slide the column window
+#pragma unroll
+        for (int k = 0; k < VB; ++k)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                pm[k][q] = pc[k][q];
+                pc[k][q] = pp[k][q];
+                pp[k][q] = pn[k][q];
+            }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) wzm[q] = wz[q];
     }
 }
 
@@ -403,6 +496,45 @@ template <int VP, int WF, int VB, bool A16> cudaError_t step_il_launch(const Ste
     return cudaGetLastError();
 }
 
+template <int VP, int WF, int VB, bool A16> cudaError_t step_zm_launch(const StepArgs &a)
+{
+    const int tx = a.nvec / VB;
+    const int spb = il_spb(tx, a.threads);
+    dim3 block(tx, spb);
+    dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.nblk);
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    k_step_zm<VP, WF, VB, A16><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g, a.nvec);
+    return cudaGetLastError();
+}
+
+template <int VP, int WF> cudaError_t step_zm_w(const StepArgs &a)
+{
+    if constexpr (!combo_ok<VP, WF>()) {
+        return cudaErrorNotSupported;
+    } else {
+        if (a.nvec < 1 || a.nvec > 256) return cudaErrorInvalidValue;
+        int vb = a.vb > 0 ? a.vb : 1;
+        if (a.nvec % vb != 0) vb = 1;
+        if constexpr (VP == P_F32) {
+            const bool a16 = (a.nvec % 2 == 0);
+            switch (vb) {
+            case 2: return a16 ? step_zm_launch<VP, WF, 2, true>(a) : step_zm_launch<VP, WF, 2, false>(a);
+            case 4: return a16 ? step_zm_launch<VP, WF, 4, true>(a) : step_zm_launch<VP, WF, 4, false>(a);
+            default: return step_zm_launch<VP, WF, 1, false>(a);
+            }
+        } else if constexpr (VP == P_F64) {
+            if (vb == 2) return step_zm_launch<VP, WF, 2, false>(a);
+            return step_zm_launch<VP, WF, 1, false>(a);
+        } else {
+            switch (vb) {
+            case 2: return step_zm_launch<VP, WF, 2, false>(a);
+            case 4: return step_zm_launch<VP, WF, 4, false>(a);
+            default: return step_zm_launch<VP, WF, 1, false>(a);
+            }
+        }
+    }
+}
+
 // vb = vectors per thread; it must divide nvec (else 1 is used).  FP32 groups
 // of an even count on an even nvec are 16-byte aligned.
 template <int VP, int WF> cudaError_t step_il_w(const StepArgs &a)
@@ -505,6 +637,12 @@ template <int VP> cudaError_t step_il_dispatch(const StepArgs &a)
 {
     const int wf = a.wfmt;
     TLS_WFMT_SWITCH(step_il_w, VP, (a), cudaErrorNotSupported)
+}
+
+template <int VP> cudaError_t step_zm_dispatch(const StepArgs &a)
+{
+    const int wf = a.wfmt;
+    TLS_WFMT_SWITCH(step_zm_w, VP, (a), cudaErrorNotSupported)
 }
 
 template <int VP> cudaError_t persist_dispatch(const PersistArgs &a)

@@ -6,6 +6,7 @@ namespace tls {
 
 cudaError_t launch_step_f32(const StepArgs &a) { return step_dispatch<P_F32>(a); }
 cudaError_t launch_step_il_f32(const StepArgs &a) { return step_il_dispatch<P_F32>(a); }
+cudaError_t launch_step_zm_f32(const StepArgs &a) { return step_zm_dispatch<P_F32>(a); }
 cudaError_t launch_step_rows_f32(const StepArgs &a, int *err) { return rows_dispatch<P_F32>(a, err); }
 cudaError_t launch_persistent_f32(const PersistArgs &a) { return persist_dispatch<P_F32>(a); }
 int persistent_occupancy_f32(int wfmt, int vb, int threads) { return occ_dispatch<P_F32>(wfmt, vb, threads); }

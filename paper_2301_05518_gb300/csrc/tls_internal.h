@@ -52,6 +52,8 @@ struct PersistArgs {
 cudaError_t launch_step(const StepArgs &a);
 // Interleaved-layout multi-RHS step (nvec <= 256 vectors per record group).
 cudaError_t launch_step_il(const StepArgs &a);
+// The same step marching along z' with a register window (interleaved layout, active unused).
+cudaError_t launch_step_zm(const StepArgs &a);
 // The same step with TMA row staging in shared memory (k_rows.cuh); err gets
 // DERR_TIMEOUT if a bounded wait runs out.  rows_applicable says whether the
 // shape and formats allow it (16-byte bulk copies, CTA size, shared memory).
@@ -70,6 +72,10 @@ cudaError_t launch_step_il_f64(const StepArgs &a);
 cudaError_t launch_step_il_f32(const StepArgs &a);
 cudaError_t launch_step_il_f16(const StepArgs &a);
 cudaError_t launch_step_il_bf16(const StepArgs &a);
+cudaError_t launch_step_zm_f64(const StepArgs &a);
+cudaError_t launch_step_zm_f32(const StepArgs &a);
+cudaError_t launch_step_zm_f16(const StepArgs &a);
+cudaError_t launch_step_zm_bf16(const StepArgs &a);
 cudaError_t launch_step_rows_f64(const StepArgs &a, int *err);
 cudaError_t launch_step_rows_f32(const StepArgs &a, int *err);
 cudaError_t launch_step_rows_f16(const StepArgs &a, int *err);

@@ -32,6 +32,8 @@ std::vector<Cand> candidates(int nvec, int storage, bool rows)
         for (int t : {64, 128, 256})
             if (t >= G / vb || t == 256) c.push_back({TLS_KERNEL_MRHS, vb, t});
         if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0});
+        for (int t : {128, 256})
+            if (t >= G / vb || t == 256) c.push_back({TLS_KERNEL_MRHS_ZM, vb, t});
     }
     const int vmax = storage == TLS_F64 ? 4 : 8;
     for (int vb : {1, 4, 8})
@@ -51,7 +53,7 @@ tls_status tls_tune_set(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
                         const tls_tune_entry *entry)
 {
     if (!ctx || !entry) return fail(TLS_ERR_ARG, "tls_tune_set: NULL argument");
-    if (entry->kernel < TLS_KERNEL_SINGLE || entry->kernel > TLS_KERNEL_MRHS_ROWS)
+    if (entry->kernel < TLS_KERNEL_SINGLE || entry->kernel > TLS_KERNEL_MRHS_ZM)
         return fail(TLS_ERR_ARG, "tls_tune_set: kernel %d", entry->kernel);
     std::lock_guard<FairMutex> lk(ctx->mu);
     auto it = ctx->gauges.find(id);

@@ -39,6 +39,7 @@ TLS_F64, TLS_F32, TLS_F16, TLS_BF16 = 0, 1, 2, 3
 TLS_R18, TLS_R12, TLS_R8 = 18, 12, 8
 TLS_KERNEL_AUTO, TLS_KERNEL_SINGLE, TLS_KERNEL_MRHS, TLS_KERNEL_PERSISTENT = 0, 1, 2, 3
 TLS_KERNEL_MRHS_ROWS = 4
+TLS_KERNEL_MRHS_ZM = 5
 TLS_ALL_T = -1
 
 #: every symbol include/tls.h declares

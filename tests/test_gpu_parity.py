@@ -377,23 +377,30 @@ def test_interleaved_groups_bitwise_equal_planar(ctx, T, nvec):
     assert np.array_equal(na, nb)
 
 
+@pytest.mark.parametrize("kname", ["MRHS_ROWS", "MRHS_ZM"])
 @pytest.mark.parametrize("dims,nvec,storage", [((8, 8, 8, 3), 5, "F32"), ((16, 8, 8, 2), 24, "F32"),
                                                ((8, 16, 24, 2), 6, "F16"), ((8, 8, 8, 2), 3, "BF16"),
                                                ((6, 4, 8, 2), 4, "F32"), ((8, 4, 4, 1), 300, "F32"),
-                                               ((24, 8, 8, 1), 2, "F16")])
-def test_rows_kernel_bitwise_equal_single(ctx, T, dims, nvec, storage):
-    """TMA row-staged multi-RHS kernel == one vector per launch, bitwise (falls back when hx % 4 != 0)."""
+                                               ((24, 8, 8, 1), 2, "F16"), ((4, 4, 2, 2), 6, "F32"),
+                                               ((2, 2, 2, 1), 2, "F32")])
+def test_rows_and_zm_kernels_bitwise_equal_single(ctx, T, kname, dims, nvec, storage):
+    """TMA row-staged and z-marching multi-RHS kernels == one vector per launch, bitwise.
+
+    The row kernel falls back to the interleaved kernel when hx % 4 != 0; the
+    shapes include hz = 1 and hz = 2 (z-window wrap) and L = 2.
+    """
     U = gauge(dims, "haar", 31)
     vecs = synth.gaussian_vectors(dims, nvec, 32, dtype=torch.complex64)
     st = getattr(T, "TLS_" + storage)
+    kk = getattr(T, "TLS_KERNEL_" + kname)
     for t0 in (-1, 1 if dims[3] > 1 else 0):
-        a, na = _run(ctx, T, U, dims, vecs, st, T.TLS_F32, 18, T.TLS_KERNEL_MRHS_ROWS, 5, 1.1, t0)
+        a, na = _run(ctx, T, U, dims, vecs, st, T.TLS_F32, 18, kk, 5, 1.1, t0)
         b, nb = _run(ctx, T, U, dims, vecs, st, T.TLS_F32, 18, T.TLS_KERNEL_SINGLE, 5, 1.1, t0)
         assert np.array_equal(a, b)
         assert np.array_equal(na, nb)
     if storage == "F32":
         want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), 5, 1.1)
-        a, _ = _run(ctx, T, U, dims, vecs, st, T.TLS_F32, 18, T.TLS_KERNEL_MRHS_ROWS, 5, 1.1, -1)
+        a, _ = _run(ctx, T, U, dims, vecs, st, T.TLS_F32, 18, kk, 5, 1.1, -1)
         assert max(per_vector_rel_l2(a, want)) <= 2e-6 * 5
 
 
