@@ -227,6 +227,8 @@ typedef struct {
     int kernel;             /* TLS_KERNEL_SINGLE, _MRHS or _PERSISTENT         */
     int vecs_per_thread;    /* vectors per thread (planar kernels)             */
     int threads;            /* threads per CTA                                 */
+    int tile[3];            /* multi-RHS kernel: sites per CTA along x', y',   */
+                            /* z' of a sublattice (0 = a strip along x')       */
     double ms_per_step;     /* measured time of one smearing step              */
 } tls_tune_entry;
 

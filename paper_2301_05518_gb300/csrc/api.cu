@@ -481,7 +481,7 @@ tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int
                      double width, int timeslice, int storage, int kernel, void *stream, double *norms_out)
 {
     return smear_impl(ctx, id, vecs, io_prec, vecs_on_device, nvec, N, width, timeslice, storage, kernel, 0, 0,
-                      stream, norms_out);
+                      nullptr, stream, norms_out);
 }
 
 }  // extern "C"
@@ -490,7 +490,7 @@ namespace tls {
 
 tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec, int N,
                       double width, int timeslice, int storage, int kernel, int force_vb, int force_threads,
-                      void *stream, double *norms_out)
+                      const int *force_tile, void *stream, double *norms_out)
 {
     if (!ctx || !vecs) return fail(TLS_ERR_ARG, "tls_smear: NULL argument");
     if (io_prec != TLS_F64 && io_prec != TLS_F32)
@@ -526,6 +526,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     int kern = kernel;
     int vb = 0;
     int threads = 0;
+    int tile[3] = {0, 0, 0};
     {
         TuneKey key{{gg->L[0], gg->L[1], gg->L[2], gg->L[3]}, nsl, nvec, storage, gg->wfmt};
         auto it = ctx->tune.find(key);
@@ -536,10 +537,13 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         if (have && it->second.kernel == kern) {
             vb = it->second.vb;
             threads = it->second.threads;
+            for (int k = 0; k < 3; ++k) tile[k] = it->second.tile[k];
         }
     }
     if (force_vb > 0) vb = force_vb;
     if (force_threads > 0) threads = force_threads;
+    if (force_tile)
+        for (int k = 0; k < 3; ++k) tile[k] = force_tile[k];
     const int G0 = std::min(nvec, 256);
     if (kern == TLS_KERNEL_SINGLE) {
         vb = 1;
@@ -717,6 +721,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
                 sa.threads = threads;
                 sa.stream = st;
                 sa.vstride_in = sa.vstride_out = vs;
+                for (int k = 0; k < 3; ++k) sa.tile[k] = tile[k];
                 const int sub_groups = kern == TLS_KERNEL_SINGLE ? gn : 1;
                 sa.nvec = kern == TLS_KERNEL_SINGLE ? 1 : gn;
                 for (int gi = 0; gi < sub_groups && e == cudaSuccess; ++gi) {

@@ -84,6 +84,7 @@ struct TuneKey {
 };
 struct TuneVal {
     int kernel, vb, threads;
+    int tile[3];
     double ms;
 };
 
@@ -141,7 +142,7 @@ int default_il_vb(int storage, int nvec);
 // tls_smear with an optional forced vectors-per-thread / threads (0 = planner's choice).
 tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec, int N,
                       double width, int timeslice, int storage, int kernel, int force_vb, int force_threads,
-                      void *stream, double *norms_out);
+                      const int *force_tile, void *stream, double *norms_out);
 
 // The serving subsystem (serve.cpp).
 void serve_shutdown(tls_ctx *ctx);

@@ -25,6 +25,7 @@ struct StepArgs {
     int prec_out;          // vector storage of `out`
     int vb;                // vectors per thread
     int threads;           // threads per CTA (multiple of 32)
+    int tile[3];           // interleaved kernel: sites per CTA along x', y', z' (0 = a strip along x')
     cudaStream_t stream;
 };
 

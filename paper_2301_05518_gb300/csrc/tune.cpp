@@ -17,27 +17,33 @@ namespace {
 
 struct Cand {
     int kernel, vb, threads;
+    int tile[3];
 };
 
 std::vector<Cand> candidates(int nvec, int storage, bool rows)
 {
     std::vector<Cand> c;
     if (nvec <= 4) {
-        c.push_back({TLS_KERNEL_SINGLE, 1, 128});
-        c.push_back({TLS_KERNEL_SINGLE, 1, 256});
+        c.push_back({TLS_KERNEL_SINGLE, 1, 128, {0, 0, 0}});
+        c.push_back({TLS_KERNEL_SINGLE, 1, 256, {0, 0, 0}});
     }
     const int G = std::min(nvec, 256);
     for (int vb : {1, 2, 4}) {
         if (G % vb != 0 || (storage == TLS_F64 && vb > 2)) continue;
+        const int tx = G / vb;
         for (int t : {64, 128, 256})
-            if (t >= G / vb || t == 256) c.push_back({TLS_KERNEL_MRHS, vb, t});
-        if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0});
-        for (int t : {128, 256})
-            if (t >= G / vb || t == 256) c.push_back({TLS_KERNEL_MRHS_ZM, vb, t});
+            if (t >= tx || t == 256) c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 0, 0}});
+        // 3-D site tiles: more of each site's neighbours are records this CTA reads anyway
+        static const int tiles[][3] = {{2, 2, 2}, {4, 2, 2}, {4, 4, 1}, {4, 4, 2}, {8, 2, 2}, {2, 4, 4}};
+        for (const auto &tl : tiles) {
+            const int sites = tl[0] * tl[1] * tl[2];
+            if (tx * sites <= 512 && tx * sites >= 64) c.push_back({TLS_KERNEL_MRHS, vb, 0, {tl[0], tl[1], tl[2]}});
+        }
+        if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0, {0, 0, 0}});
     }
     const int vmax = storage == TLS_F64 ? 4 : 8;
     for (int vb : {1, 4, 8})
-        if (vb <= vmax && (vb == 1 || vb <= 2 * nvec)) c.push_back({TLS_KERNEL_PERSISTENT, vb, 256});
+        if (vb <= vmax && (vb == 1 || vb <= 2 * nvec)) c.push_back({TLS_KERNEL_PERSISTENT, vb, 256, {0, 0, 0}});
     return c;
 }
 
@@ -62,7 +68,8 @@ tls_status tls_tune_set(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
     if (!gg.built) return fail(TLS_ERR_NOT_BUILT, "tls_tune_set: W not built");
     const int nsl = timeslice < 0 ? gg.L[3] : 1;
     TuneKey key{{gg.L[0], gg.L[1], gg.L[2], gg.L[3]}, nsl, nvec, storage, gg.wfmt};
-    ctx->tune[key] = TuneVal{entry->kernel, entry->vecs_per_thread, entry->threads, entry->ms_per_step};
+    ctx->tune[key] = TuneVal{entry->kernel, entry->vecs_per_thread, entry->threads,
+                             {entry->tile[0], entry->tile[1], entry->tile[2]}, entry->ms_per_step};
     return ok();
 }
 
@@ -89,7 +96,7 @@ tls_status tls_autotune(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
     cudaMemset(tmp, 0, bytes);
     const bool was = ctx->profiling;
     ctx->profiling = true;
-    TuneVal win{0, 0, 0, 1e300};
+    TuneVal win{0, 0, 0, {0, 0, 0}, 1e300};
     int n = 0;
     const int G = std::min(nvec, 256);
     const bool rows = storage != TLS_F64 && rows_applicable(gg.wfmt, storage, gg.g, G, 1, ctx->max_smem);
@@ -97,19 +104,19 @@ tls_status tls_autotune(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
         if (c.kernel == TLS_KERNEL_MRHS_ROWS && !rows_applicable(gg.wfmt, storage, gg.g, G, c.vb, ctx->max_smem))
             continue;
         // one warm-up call, then the timed one
-        s = smear_impl(ctx, id, tmp, io, 1, nvec, 1, 0.5, timeslice, storage, c.kernel, c.vb, c.threads, nullptr,
-                       nullptr);
+        s = smear_impl(ctx, id, tmp, io, 1, nvec, 1, 0.5, timeslice, storage, c.kernel, c.vb, c.threads, c.tile,
+                       nullptr, nullptr);
         if (s == TLS_OK)
             s = smear_impl(ctx, id, tmp, io, 1, nvec, steps, 0.5 * steps, timeslice, storage, c.kernel, c.vb,
-                           c.threads, nullptr, nullptr);
+                           c.threads, c.tile, nullptr, nullptr);
         if (s != TLS_OK) {
             if (s == TLS_ERR_UNSUPPORTED) continue;
             break;
         }
         const double ms = ctx->prof.ms_iter / steps;
-        if (all && n < max_all) all[n] = tls_tune_entry{c.kernel, c.vb, c.threads, ms};
+        if (all && n < max_all) all[n] = tls_tune_entry{c.kernel, c.vb, c.threads, {c.tile[0], c.tile[1], c.tile[2]}, ms};
         ++n;
-        if (ms < win.ms) win = TuneVal{c.kernel, c.vb, c.threads, ms};
+        if (ms < win.ms) win = TuneVal{c.kernel, c.vb, c.threads, {c.tile[0], c.tile[1], c.tile[2]}, ms};
     }
     ctx->profiling = was;
     dev_free(ctx, tmp, bytes);
@@ -117,7 +124,7 @@ tls_status tls_autotune(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
     if (win.kernel == 0) return fail(TLS_ERR_UNSUPPORTED, "tls_autotune: no candidate ran");
     TuneKey key{{gg.L[0], gg.L[1], gg.L[2], gg.L[3]}, nsl, nvec, storage, gg.wfmt};
     ctx->tune[key] = win;
-    if (best) *best = tls_tune_entry{win.kernel, win.vb, win.threads, win.ms};
+    if (best) *best = tls_tune_entry{win.kernel, win.vb, win.threads, {win.tile[0], win.tile[1], win.tile[2]}, win.ms};
     if (n_all) *n_all = n;
     return ok();
 }

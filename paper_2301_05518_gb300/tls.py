@@ -64,7 +64,7 @@ class tls_profile(ctypes.Structure):
 
 class tls_tune_entry(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("vecs_per_thread", ctypes.c_int), ("threads", ctypes.c_int),
-                ("ms_per_step", ctypes.c_double)]
+                ("tile", ctypes.c_int * 3), ("ms_per_step", ctypes.c_double)]
 
 
 class tls_serve_opts(ctypes.Structure):
@@ -245,7 +245,7 @@ def tls_set_barrier_budget(ctx, polls: int) -> None:
 
 def _entry(e):
     return {"kernel": e.kernel, "vecs_per_thread": e.vecs_per_thread, "threads": e.threads,
-            "ms_per_step": e.ms_per_step}
+            "tile": list(e.tile), "ms_per_step": e.ms_per_step}
 
 
 def tls_autotune(ctx, gauge: int, nvec: int, storage: int, timeslice: int = TLS_ALL_T, steps: int = 4):
@@ -259,8 +259,8 @@ def tls_autotune(ctx, gauge: int, nvec: int, storage: int, timeslice: int = TLS_
 
 
 def tls_tune_set(ctx, gauge: int, nvec: int, storage: int, timeslice: int, kernel: int,
-                 vecs_per_thread: int = 1, threads: int = 256) -> None:
-    e = tls_tune_entry(int(kernel), int(vecs_per_thread), int(threads), 0.0)
+                 vecs_per_thread: int = 1, threads: int = 256, tile=(0, 0, 0)) -> None:
+    e = tls_tune_entry(int(kernel), int(vecs_per_thread), int(threads), (ctypes.c_int * 3)(*tile), 0.0)
     _check(lib.tls_tune_set(ctx, int(gauge), int(nvec), int(storage), int(timeslice), ctypes.byref(e)))
 
 
@@ -355,8 +355,8 @@ class Context:
     def autotune(self, gauge, nvec, storage, timeslice=TLS_ALL_T, steps=4):
         return tls_autotune(self.h, gauge, nvec, storage, timeslice, steps)
 
-    def tune_set(self, gauge, nvec, storage, timeslice, kernel, vecs_per_thread=1, threads=256):
-        return tls_tune_set(self.h, gauge, nvec, storage, timeslice, kernel, vecs_per_thread, threads)
+    def tune_set(self, gauge, nvec, storage, timeslice, kernel, vecs_per_thread=1, threads=256, tile=(0, 0, 0)):
+        return tls_tune_set(self.h, gauge, nvec, storage, timeslice, kernel, vecs_per_thread, threads, tile)
 
     def bytes_in_use(self):
         return tls_bytes_in_use(self.h)

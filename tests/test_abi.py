@@ -66,8 +66,9 @@ def test_create_without_gpu_reports_error(libpath):
 def test_struct_sizes_match_header(libpath):
     """ctypes mirrors of the public structs have the C sizes (checked with gcc)."""
     from paper_2301_05518_gb300 import tls
-    src = ('#include "tls.h"\n#include <stdio.h>\nint main(){printf("%zu %zu %zu %zu\\n",'
-           'sizeof(tls_profile),sizeof(tls_serve_opts),sizeof(tls_job),sizeof(tls_job_result));}\n')
+    src = ('#include "tls.h"\n#include <stdio.h>\nint main(){printf("%zu %zu %zu %zu %zu\\n",'
+           'sizeof(tls_profile),sizeof(tls_serve_opts),sizeof(tls_job),sizeof(tls_job_result),'
+           'sizeof(tls_tune_entry));}\n')
     import tempfile
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "s.c")
@@ -76,4 +77,5 @@ def test_struct_sizes_match_header(libpath):
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         sizes = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     assert sizes == [ctypes.sizeof(tls.tls_profile), ctypes.sizeof(tls.tls_serve_opts),
-                     ctypes.sizeof(tls.tls_job), ctypes.sizeof(tls.tls_job_result)]
+                     ctypes.sizeof(tls.tls_job), ctypes.sizeof(tls.tls_job_result),
+                     ctypes.sizeof(tls.tls_tune_entry)]

@@ -418,3 +418,21 @@ def test_rows_kernel_at_headline_shape_sampled(ctx, T):
     for v, src in ref.items():
         want = oracle.smear(W, src, 8, 1.6)
         assert rel_l2(vecs[v, 1:2].cpu().numpy().astype(np.complex128), want) <= 2e-6 * 8
+
+
+@pytest.mark.parametrize("tile,vb", [((2, 2, 2), 2), ((4, 4, 2), 1), ((8, 2, 2), 4), ((3, 5, 2), 2)])
+def test_interleaved_tiles_bitwise_equal_single(ctx, T, tile, vb):
+    """3-D CTA tiles of the multi-RHS kernel, including tiles that do not divide the sublattice."""
+    dims = (12, 10, 8, 2)
+    nvec = 8
+    U = gauge(dims, "haar", 35)
+    vecs = synth.gaussian_vectors(dims, nvec, 36, dtype=torch.complex64)
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.build_twolink(gid, T.TLS_F32, 18)
+    ctx.tune_set(gid, nvec, T.TLS_F32, T.TLS_ALL_T, T.TLS_KERNEL_MRHS, vb, 0, tile)
+    a = vecs.clone().cuda()
+    ctx.smear(gid, a, T.TLS_F32, nvec, 6, 1.3, storage=T.TLS_F32, kernel=T.TLS_KERNEL_AUTO)
+    b = vecs.clone().cuda()
+    ctx.smear(gid, b, T.TLS_F32, nvec, 6, 1.3, storage=T.TLS_F32, kernel=T.TLS_KERNEL_SINGLE)
+    ctx.free_gauge(gid)
+    assert torch.equal(a, b)
