@@ -65,6 +65,14 @@ def dist_setup(backend):
     return ws, rank, local
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per lattice site of
+# one launch of the dominant kernel, from the ncu captures summarised in
+# profiles/ (64^3x4 lattice, 24 vectors, FP32, W FP32-18; the full 64^3x96 launch
+# scales by the number of sites).  Keyed by (kernel, vectors per thread,
+# tile); a configuration without a capture of its current code reports null.
+PROFILED_TRAFFIC_PER_SITE = {}
+
+
 def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
     """The largest value of x over all ranks (the job is as slow as its slowest rank)."""
     if ws <= 1:
@@ -416,8 +424,12 @@ def our_arm(args):
     per_launch_bytes = prof_last["iter_bytes"] / max(1, iter_launches)
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
     kern_name = {1: "single", 2: "mrhs", 3: "persistent", 4: "mrhs_rows", 5: "mrhs_zm"}.get(prof_last["kernel"], "?")
+    tune_best = tune["best"] if tune else {}
+    tkey = (kern_name, prof_last["vecs_per_thread"], tuple(tune_best.get("tile", (0, 0, 0))))
+    per_site = PROFILED_TRAFFIC_PER_SITE.get(tkey) if nvec == 24 and storage == T.TLS_F32 else None
+    traffic = per_site * V if per_site else None  # bytes per launch (one step over all sites)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": None,
+            "frac": achieved / hbm_peak, "traffic": traffic,
             "kernel": {"persistent": "k_persist", "mrhs": "k_step_il", "mrhs_rows": "k_step_rows",
                        "mrhs_zm": "k_step_zm", "single": "k_step"}.get(kern_name, "?"),
             "peak_source": peak_kind,

@@ -124,6 +124,13 @@ tls_status tls_load_gauge(tls_ctx *ctx, const double *U, int nd, const int dims[
 tls_status tls_build_twolink(tls_ctx *ctx, tls_gauge_id id, int wprec, int recon,
                              int keep_U, void *stream);
 
+/* ---- one-link field (Sec. 2, Eq. 2: the links U_mu of the hopping term) -----
+ * Stores the spatial links U_mu(x) themselves, rounded to nearest in `prec`
+ * (TLS_F64 or TLS_F32), in the two-link field's layout, for
+ * tls_smear_onelink.  keep_U = 0 releases the FP64 device copy of U.
+ * Errors: TLS_ERR_NOT_FOUND, TLS_ERR_STATE (U released), TLS_ERR_UNSUPPORTED. */
+tls_status tls_build_links(tls_ctx *ctx, tls_gauge_id id, int prec, int keep_U, void *stream);
+
 /* Releases U, W and everything cached for gauge `id`. */
 tls_status tls_free_gauge(tls_ctx *ctx, tls_gauge_id id);
 
@@ -167,6 +174,18 @@ tls_status tls_export_gauge(tls_ctx *ctx, tls_gauge_id id, double *out, int on_d
 tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec,
                      int vecs_on_device, int nvec, int N, double width, int timeslice,
                      int storage, int kernel, void *stream, double *norms_out);
+
+/* ---- one-link Gaussian smearing (Sec. 2, Eq. 2-3) ---------------------------
+ * Applies psi <- C (1 + alpha H)^N psi with C = 1 (Eq. 3), where
+ *     H psi(x) = sum_mu [ U_mu(x) psi(x + mu) + U_mu^dag(x - mu) psi(x - mu) ]
+ * is the one-link hopping operator of Eq. 2 (mu = x, y, z; periodic), each
+ * step psi' = psi + alpha H psi out of place.  The Laplacian form of Eq. 4,
+ * C' (1 + alpha' Lap)^N, is the same operator with alpha = alpha'/(1 - 6 alpha')
+ * and C' = (1 + 6 alpha)^N.  Needs tls_build_links (FP64 links for TLS_F64
+ * storage, FP32 links otherwise).  Vectors, slices, storage, norms and errors
+ * as tls_smear (multi-right-hand-side kernel, interleaved layout).          */
+tls_status tls_smear_onelink(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec,
+                             int N, double alpha, int timeslice, int storage, void *stream, double *norms_out);
 
 /* ---- smearing without any device allocation --------------------------------
  * The paper has no counterpart to this entry point.  It serves callers that
@@ -227,8 +246,8 @@ typedef struct {
     int kernel;             /* TLS_KERNEL_SINGLE, _MRHS or _PERSISTENT         */
     int vecs_per_thread;    /* vectors per thread (planar kernels)             */
     int threads;            /* threads per CTA                                 */
-    int tile[3];            /* multi-RHS kernel: sites per CTA along x', y',   */
-                            /* z' of a sublattice (0 = a strip along x')       */
+    int tile[3];            /* multi-RHS kernel: tile[0] > 0 sets the sites    */
+                            /* per CTA (a strip along x'); tile[1..2] unused   */
     double ms_per_step;     /* measured time of one smearing step              */
 } tls_tune_entry;
 

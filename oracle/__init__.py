@@ -13,6 +13,8 @@ Functions (all FP64, complex numbers as numpy complex128):
 - ``apply_lap_unfused(U, psi, t0)``  same from single links        (Eq. tlLapl2)
 - ``smear(W, psi, n, sigma, t0)``    (1 + (sigma/n) Lap_two)^n psi (Eq. tlSmear)
 - ``smear_unfused(U, psi, n, sigma, t0)``
+- ``apply_hop(U, psi, t0)``         one-link hopping H psi          (Eq. 2)
+- ``smear_onelink(U, psi, n, alpha, t0)``  (1 + alpha H)^n psi     (Eq. 3, C = 1)
 
 Array shapes: ``U`` is ``[Lt, Lz, Ly, Lx, nd, 3, 3]`` (nd = 3 or 4, mu order
 x, y, z[, t]); ``W`` is ``[Lt, Lz, Ly, Lx, 3, 3, 3]``; ``psi`` is
@@ -68,6 +70,10 @@ def _load():
         lib.oracle_smear.restype = I
         lib.oracle_smear_unfused.argtypes = [P, I, P, P, I, I, D, I]
         lib.oracle_smear_unfused.restype = I
+        lib.oracle_apply_hop.argtypes = [P, I, P, P, P, I]
+        lib.oracle_apply_hop.restype = None
+        lib.oracle_smear_onelink.argtypes = [P, I, P, P, I, I, D, I]
+        lib.oracle_smear_onelink.restype = I
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = I
         _lib = lib
@@ -158,4 +164,28 @@ def smear_unfused(U, psi, n: int, sigma: float, t0: int = -1) -> np.ndarray:
                                       out.shape[0], int(n), float(sigma), int(t0))
     if rc != 0:
         raise ValueError("oracle_smear_unfused failed (%d)" % rc)
+    return out[0] if single else out
+
+
+def apply_hop(U, psi, t0: int = -1) -> np.ndarray:
+    """One-link hopping H psi (Eq. 2); unselected slices are 0."""
+    U = _c128(U)
+    psi5 = _c128(psi)
+    assert psi5.ndim == 5
+    dims = _dims(psi5.shape)
+    out = np.zeros_like(psi5)
+    _load().oracle_apply_hop(_ptr(U), U.shape[4], _ptr(dims), _ptr(psi5), _ptr(out), int(t0))
+    return out
+
+
+def smear_onelink(U, psi, n: int, alpha: float, t0: int = -1) -> np.ndarray:
+    """Gaussian smearing (1 + alpha H)^n psi (Eq. 3 with C = 1); returns a new array."""
+    U = _c128(U)
+    vecs, single = _as_vecs(psi)
+    out = vecs.copy()
+    dims = _dims(out.shape[1:])
+    rc = _load().oracle_smear_onelink(_ptr(U), U.shape[4], _ptr(dims), _ptr(out), out.shape[0], int(n),
+                                      float(alpha), int(t0))
+    if rc != 0:
+        raise ValueError("oracle_smear_onelink failed (%d)" % rc)
     return out[0] if single else out

@@ -17,6 +17,9 @@
  *                                                      (Sec. 2, Eq. tlLapl1)
  *   - the same operator from single links applied twice  (Sec. 2, Eq. tlLapl2)
  *   - psi~ = (1 + (sigma/n) Lap_two)^n psi               (Sec. 2, Eq. tlSmear)
+ *   - one-link hopping H psi(x) = sum_mu [ U_mu(x) psi(x + mu)
+ *                                   + U_mu^dag(x - mu) psi(x - mu) ]  (Sec. 2, Eq. 2)
+ *     and Gaussian smearing psi~ = C (1 + alpha H)^n psi with C = 1 (Sec. 2, Eq. 3)
  *
  * Conventions (the paper is silent on them; these are the readings used):
  *   - "Delta" below is 4 Lap_two, so one smearing step is
@@ -281,6 +284,57 @@ int oracle_smear_unfused(const double *U, int nd, const int L[4], double *psi,
         for (int it = 0; it < n; ++it) {
             oracle_apply_lap_unfused(U, nd, L, p, d, t0);
             axpy_slices(L, t0, a, d, p);
+        }
+    }
+    free(d);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One-link hopping operator of Eq. 2 on the selected slices:                */
+/*   H psi(x) = sum_mu [ U_mu(x) psi(x + mu) + U_mu^dag(x - mu) psi(x - mu) ] */
+/* ------------------------------------------------------------------------ */
+void oracle_apply_hop(const double *U, int nd, const int L[4], const double *psi, double *out, int t0)
+{
+    int tb = t0 < 0 ? 0 : t0, te = t0 < 0 ? L[3] : t0 + 1;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int t = tb; t < te; ++t)
+        for (int z = 0; z < L[2]; ++z)
+            for (int y = 0; y < L[1]; ++y)
+                for (int x = 0; x < L[0]; ++x) {
+                    long s = site_of(L, x, y, z, t);
+                    cplx acc[3], v[3];
+                    for (int c = 0; c < 3; ++c) acc[c].re = acc[c].im = 0.0;
+                    for (int mu = 0; mu < 3; ++mu) {
+                        long fwd = neighbour(L, x, y, z, t, mu, +1);
+                        long bwd = neighbour(L, x, y, z, t, mu, -1);
+                        load_vec(psi, fwd, v);
+                        add_mat_vec(link_at(U, nd, s, mu), v, acc);
+                        load_vec(psi, bwd, v);
+                        add_dag_vec(link_at(U, nd, bwd, mu), v, acc);
+                    }
+                    for (int c = 0; c < 3; ++c) {
+                        out[(s * 3 + c) * 2] = acc[c].re;
+                        out[(s * 3 + c) * 2 + 1] = acc[c].im;
+                    }
+                }
+}
+
+/* Gaussian smearing of Eq. 3 with C = 1: n steps psi <- psi + alpha H psi,   */
+/* each out of place; only the selected slices change.                        */
+int oracle_smear_onelink(const double *U, int nd, const int L[4], double *psi, int nvec, int n, double alpha,
+                         int t0)
+{
+    if (n < 0 || nvec < 0) return -1;
+    if (n == 0 || nvec == 0) return 0;
+    long vol = (long)L[0] * L[1] * L[2] * L[3];
+    double *d = (double *)calloc((size_t)vol * 6, sizeof(double));
+    if (!d) return -1;
+    for (int v = 0; v < nvec; ++v) {
+        double *p = psi + (long)v * vol * 6;
+        for (int it = 0; it < n; ++it) {
+            oracle_apply_hop(U, nd, L, p, d, t0);
+            axpy_slices(L, t0, alpha, d, p);
         }
     }
     free(d);

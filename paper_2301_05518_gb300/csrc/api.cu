@@ -144,6 +144,17 @@ cudaError_t launch_step_il(const StepArgs &a)
     }
 }
 
+cudaError_t launch_hop(const StepArgs &a)
+{
+    switch (a.prec_in) {
+    case P_F64: return launch_hop_f64(a);
+    case P_F32: return launch_hop_f32(a);
+    case P_F16: return launch_hop_f16(a);
+    case P_BF16: return launch_hop_bf16(a);
+    default: return cudaErrorNotSupported;
+    }
+}
+
 cudaError_t launch_step_zm(const StepArgs &a)
 {
     switch (a.prec_in) {
@@ -191,10 +202,13 @@ static void free_gauge(tls_ctx *ctx, Gauge &gg)
 {
     dev_free(ctx, gg.Up, gg.Up_bytes);
     dev_free(ctx, gg.W, gg.W_bytes);
+    dev_free(ctx, gg.L1, gg.L1_bytes);
     gg.Up = nullptr;
     gg.W = nullptr;
-    gg.Up_bytes = gg.W_bytes = 0;
+    gg.L1 = nullptr;
+    gg.Up_bytes = gg.W_bytes = gg.L1_bytes = 0;
     gg.built = false;
+    gg.l1fmt = -1;
 }
 
 static Gauge *find_gauge(tls_ctx *ctx, tls_gauge_id id)
@@ -418,6 +432,48 @@ tls_status tls_build_twolink(tls_ctx *ctx, tls_gauge_id id, int wprec, int recon
     return ok();
 }
 
+tls_status tls_build_links(tls_ctx *ctx, tls_gauge_id id, int prec, int keep_U, void *stream)
+{
+    if (!ctx) return fail(TLS_ERR_ARG, "tls_build_links: ctx is NULL");
+    std::lock_guard<FairMutex> lk(ctx->mu);
+    Gauge *gg = find_gauge(ctx, id);
+    if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_build_links: unknown gauge id %lld", (long long)id);
+    if (!gg->Up) return fail(TLS_ERR_STATE, "tls_build_links: the links of gauge %lld were released", (long long)id);
+    const int fmt = prec == TLS_F64 ? W_F64_18 : prec == TLS_F32 ? W_F32_18 : -1;
+    if (fmt < 0) return fail(TLS_ERR_UNSUPPORTED, "tls_build_links: precision %d (TLS_F64 or TLS_F32)", prec);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)gg->L[3] * 8 * 3 * gg->g.Ps * wfmt_bytes(fmt);
+    if (gg->L1 && gg->L1_bytes != bytes) {
+        dev_free(ctx, gg->L1, gg->L1_bytes);
+        gg->L1 = nullptr;
+        gg->L1_bytes = 0;
+    }
+    if (!gg->L1) {
+        tls_status s = dev_alloc(ctx, (void **)&gg->L1, bytes, "tls_build_links: link field");
+        if (s != TLS_OK) return s;
+        gg->L1_bytes = bytes;
+        cudaMemsetAsync(gg->L1, 0, bytes, st);
+    }
+    cudaError_t e = launch_build_links(gg->Up, gg->L1, fmt, gg->g, gg->L[3] * 8, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "tls_build_links");
+    gg->l1fmt = fmt;
+    if (!keep_U) {
+        dev_free(ctx, gg->Up, gg->Up_bytes);
+        gg->Up = nullptr;
+        gg->Up_bytes = 0;
+    }
+    return ok();
+}
+
+tls_status tls_smear_onelink(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec,
+                             int N, double alpha, int timeslice, int storage, void *stream, double *norms_out)
+{
+    return smear_impl(ctx, id, vecs, io_prec, vecs_on_device, nvec, N, alpha, timeslice, storage, TLS_KERNEL_MRHS, 0,
+                      0, nullptr, stream, norms_out, 1);
+}
+
 tls_status tls_free_gauge(tls_ctx *ctx, tls_gauge_id id)
 {
     if (!ctx) return fail(TLS_ERR_ARG, "tls_free_gauge: ctx is NULL");
@@ -490,7 +546,7 @@ namespace tls {
 
 tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec, int N,
                       double width, int timeslice, int storage, int kernel, int force_vb, int force_threads,
-                      const int *force_tile, void *stream, double *norms_out)
+                      const int *force_tile, void *stream, double *norms_out, int op)
 {
     if (!ctx || !vecs) return fail(TLS_ERR_ARG, "tls_smear: NULL argument");
     if (io_prec != TLS_F64 && io_prec != TLS_F32)
@@ -503,11 +559,24 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     std::lock_guard<FairMutex> lk(ctx->mu);
     Gauge *gg = find_gauge(ctx, id);
     if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_smear: unknown gauge id %lld", (long long)id);
-    if (!gg->built) return fail(TLS_ERR_NOT_BUILT, "tls_smear: tls_build_twolink has not run for gauge %lld", (long long)id);
+    if (op == 0 && !gg->built)
+        return fail(TLS_ERR_NOT_BUILT, "tls_smear: tls_build_twolink has not run for gauge %lld", (long long)id);
+    if (op == 1 && !gg->L1)
+        return fail(TLS_ERR_NOT_BUILT, "tls_smear_onelink: tls_build_links has not run for gauge %lld", (long long)id);
     if (timeslice < TLS_ALL_T || timeslice >= gg->L[3])
         return fail(TLS_ERR_ARG, "tls_smear: timeslice %d outside [-1, %d)", timeslice, gg->L[3]);
-    tls_status s = check_smear_combo(*gg, storage);
-    if (s != TLS_OK) return s;
+    tls_status s = TLS_OK;
+    if (op == 0) {
+        s = check_smear_combo(*gg, storage);
+        if (s != TLS_OK) return s;
+    } else {
+        const bool okc = storage == TLS_F64 ? gg->l1fmt == W_F64_18 : gg->l1fmt == W_F32_18;
+        if (storage < TLS_F64 || storage > TLS_BF16) return fail(TLS_ERR_ARG, "tls_smear_onelink: storage %d", storage);
+        if (!okc)
+            return fail(TLS_ERR_UNSUPPORTED, "tls_smear_onelink: storage %d with link format %d", storage, gg->l1fmt);
+    }
+    const int fmt = op == 0 ? gg->wfmt : gg->l1fmt;
+    const char *field = op == 0 ? gg->W : gg->L1;
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
 
@@ -544,17 +613,21 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     if (force_threads > 0) threads = force_threads;
     if (force_tile)
         for (int k = 0; k < 3; ++k) tile[k] = force_tile[k];
+    if (op == 1) {  // one-link hops: the interleaved kernel only
+        kern = TLS_KERNEL_MRHS;
+        for (int k = 0; k < 3; ++k) tile[k] = 0;
+    }
     const int G0 = std::min(nvec, 256);
     if (kern == TLS_KERNEL_SINGLE) {
         vb = 1;
         if (threads <= 0) threads = 128;
     } else if (kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS || kern == TLS_KERNEL_MRHS_ZM) {
         if (vb <= 0 || vb > 4 || G0 % vb != 0 || (storage == TLS_F64 && vb > 2)) vb = default_il_vb(storage, G0);
-        if (threads <= 0) threads = 256;
+        if (threads == 0) threads = 256;  // < 0: the register-capped variant
         // TMA row staging needs 16-byte copies and a row that fits in shared memory
         if (kern == TLS_KERNEL_MRHS_ROWS &&
-            !(rows_applicable(gg->wfmt, storage, gg->g, G0, vb, ctx->max_smem) &&
-              rows_applicable(gg->wfmt, storage, gg->g, nvec % G0 ? nvec % G0 : G0, vb, ctx->max_smem)))
+            !(rows_applicable(fmt, storage, gg->g, G0, vb, ctx->max_smem) &&
+              rows_applicable(fmt, storage, gg->g, nvec % G0 ? nvec % G0 : G0, vb, ctx->max_smem)))
             kern = TLS_KERNEL_MRHS;
     } else {
         if (vb <= 0) vb = default_vb(storage, nvec);
@@ -602,10 +675,10 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     PersistArgs pa{};
     if (kern == TLS_KERNEL_PERSISTENT && N > 0) {
         const int sprec = storage == TLS_F64 ? P_F64 : P_F32;
-        const int occ = persistent_occupancy(gg->wfmt, storage, sprec, vb, threads);
+        const int occ = persistent_occupancy(fmt, storage, sprec, vb, threads);
         if (occ <= 0) return fail(TLS_ERR_UNSUPPORTED, "tls_smear: persistent kernel cannot be resident");
         const int SBY = vfmt_bytes(sprec);
-        const double per_blk = (double)g.Ps * (3.0 * wfmt_bytes(gg->wfmt) + 2.0 * nvec * SBY);
+        const double per_blk = (double)g.Ps * (3.0 * wfmt_bytes(fmt) + 2.0 * nvec * SBY);
         const double budget = 48.0 * (1 << 20);
         int gb = (int)std::max(1.0, std::floor(budget / per_blk));
         const int64_t want_items = (int64_t)occ * ctx->num_sms * threads;
@@ -622,7 +695,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         pa.sprec = sprec;
     }
 
-    const double a = N > 0 ? width / (4.0 * N) : 0.0;
+    const double a = N > 0 ? (op == 0 ? width / (4.0 * N) : width) : 0.0;
     for (int v = 0; v < nvec; ++v) ctx->h_alpha[v] = a;
 
     cudaError_t e = cudaSuccess;
@@ -668,7 +741,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     mark(1);
     if (prof) t_h2d = lap(0, 1);
 
-    const char *W0 = gg->W + (size_t)t_first * 8 * 3 * g.Ps * wfmt_bytes(gg->wfmt);
+    const char *W0 = field + (size_t)t_first * 8 * 3 * g.Ps * wfmt_bytes(fmt);
     const size_t io_vec_bytes = (size_t)io_vstride_sites * 6 * io_elem;
     for (int g0 = 0; g0 < nvec && e == cudaSuccess; g0 += G) {
         const int gn = std::min(G, nvec - g0);
@@ -697,7 +770,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
                 pa.nvec = gn;
                 pa.N = N;
                 pa.vstride = vs;
-                pa.wfmt = gg->wfmt;
+                pa.wfmt = fmt;
                 pa.prec = storage;
                 pa.vb = vb;
                 pa.threads = threads;
@@ -715,7 +788,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
                 sa.W = W0;
                 sa.g = g;
                 sa.nblk = nblk;
-                sa.wfmt = gg->wfmt;
+                sa.wfmt = fmt;
                 sa.prec_in = sa.prec_out = storage;
                 sa.vb = vb;
                 sa.threads = threads;
@@ -731,7 +804,8 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
                         sa.in = (it & 1) ? y : x;
                         sa.out = (it & 1) ? x : y;
                         sa.alpha = alpha_g + gi;
-                        e = kern == TLS_KERNEL_MRHS_ROWS ? launch_step_rows(sa, ctx->d_err)
+                        e = op == 1                     ? launch_hop(sa)
+                            : kern == TLS_KERNEL_MRHS_ROWS ? launch_step_rows(sa, ctx->d_err)
                             : kern == TLS_KERNEL_MRHS_ZM ? launch_step_zm(sa)
                             : il                         ? launch_step_il(sa)
                                                          : launch_step(sa);
@@ -793,10 +867,10 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         p.launches = launches;
         p.iter_launches = iter_launches;
         const double sites = (double)nblk * g.Vs;
-        const double wb = 3.0 * wfmt_bytes(gg->wfmt), vbb = 2.0 * VBY;
+        const double wb = 3.0 * wfmt_bytes(fmt), vbb = 2.0 * VBY;
         p.iter_bytes = kern == TLS_KERNEL_SINGLE ? (double)N * nvec * sites * (wb + vbb)
                                                  : (double)N * sites * (wb * ((nvec + G - 1) / G) + nvec * vbb);
-        p.iter_flops = 450.0 * N * nvec * sites;
+        p.iter_flops = (op == 0 ? 450.0 : 438.0) * N * nvec * sites;
         p.kernel = kern;
         p.vecs_per_thread = vb;
     }

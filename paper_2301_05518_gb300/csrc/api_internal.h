@@ -67,6 +67,9 @@ struct Gauge {
     size_t W_bytes = 0;
     int wfmt = -1;
     bool built = false;
+    char *L1 = nullptr;    // one-link field (Eq. 2 links, rounded), W planes
+    size_t L1_bytes = 0;
+    int l1fmt = -1;
 };
 
 // Best kernel per problem shape, filled by tls_autotune-style measurement.
@@ -139,10 +142,12 @@ int default_vb(int storage, int nvec);
 // Vectors per thread of the interleaved multi-RHS kernel (a divisor of nvec).
 int default_il_vb(int storage, int nvec);
 
-// tls_smear with an optional forced vectors-per-thread / threads (0 = planner's choice).
+// tls_smear with an optional forced vectors-per-thread / threads / tile (0 = planner's choice).
+// op = 0: two-link smearing (Eq. tlSmear, width = sigma); op = 1: one-link Gaussian
+// smearing (Eq. 3 with C = 1, width = alpha) on the link field.
 tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec, int N,
                       double width, int timeslice, int storage, int kernel, int force_vb, int force_threads,
-                      const int *force_tile, void *stream, double *norms_out);
+                      const int *force_tile, void *stream, double *norms_out, int op = 0);
 
 // The serving subsystem (serve.cpp).
 void serve_shutdown(tls_ctx *ctx);

@@ -82,7 +82,7 @@ __global__ void k_export_gauge(const double2 *__restrict__ Up, double *__restric
 // W_d(x) = U_d(x) U_d(x + d).  In sublattice terms x + d flips bit d of the
 // sublattice index, and the half coordinate advances (with wrap) only when
 // the coordinate was odd.
-template <int WF>
+template <int WF, bool ONE = false>
 __global__ void k_build_twolink(const double2 *__restrict__ Up, char *__restrict__ W, SubGeom g, int64_t total,
                                 int *err)
 {
@@ -107,6 +107,13 @@ __global__ void k_build_twolink(const double2 *__restrict__ Up, char *__restrict
         bb[k] = B[k * g.Ps];
     }
     double w[18];
+    if constexpr (ONE) {  // one-link field: U_d(x) itself
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            w[2 * k] = a[k].x;
+            w[2 * k + 1] = a[k].y;
+        }
+    } else {
 #pragma unroll
     for (int rr = 0; rr < 3; ++rr)
 #pragma unroll
@@ -123,6 +130,7 @@ __global__ void k_build_twolink(const double2 *__restrict__ Up, char *__restrict
             w[2 * (rr * 3 + cc)] = re;
             w[2 * (rr * 3 + cc) + 1] = im;
         }
+    }
     char *blk = W + ((int64_t)b * 3 + d) * g.Ps * wfmt_bytes(WF);
     if constexpr (WF == W_F32_8) {
         if (!WFmt<WF>::store(blk, g.Ps, i, w)) atomicOr(err, DERR_RECON8);
@@ -460,6 +468,20 @@ cudaError_t launch_build_twolink(const double *Up, char *W, int wfmt, const SubG
     case W_F16_12: k_build_twolink<W_F16_12><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
     case W_BF16_18: k_build_twolink<W_BF16_18><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
     case W_BF16_12: k_build_twolink<W_BF16_12><<<nb, 128, 0, s>>>(u, W, g, total, err); break;
+    default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_links(const double *Up, char *L1, int wfmt, const SubGeom &g, int nblk, cudaStream_t s)
+{
+    const int64_t total = (int64_t)nblk * 3 * g.Vs;
+    if (total == 0) return cudaSuccess;
+    const double2 *u = reinterpret_cast<const double2 *>(Up);
+    const unsigned nb = nblocks(total, 128);
+    switch (wfmt) {
+    case W_F64_18: k_build_twolink<W_F64_18, true><<<nb, 128, 0, s>>>(u, L1, g, total, nullptr); break;
+    case W_F32_18: k_build_twolink<W_F32_18, true><<<nb, 128, 0, s>>>(u, L1, g, total, nullptr); break;
     default: return cudaErrorNotSupported;
     }
     return cudaGetLastError();

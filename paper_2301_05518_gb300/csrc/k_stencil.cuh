@@ -145,24 +145,16 @@ __global__ void __launch_bounds__(256) k_step(const char *__restrict__ W, const 
 // to the planar kernels.
 // --------------------------------------------------------------------------
 template <int VP, int WF, int VB, bool A16>
-__global__ void __launch_bounds__(512) k_step_il(const char *__restrict__ W, const char *__restrict__ in,
-                                                 char *__restrict__ out, const double *__restrict__ alpha,
-                                                 const int *__restrict__ active, SubGeom g, int nvec, int tlx,
-                                                 int tly, int tlz)
+__device__ __forceinline__ void step_il_body(const char *__restrict__ W, const char *__restrict__ in,
+                                             char *__restrict__ out, const double *__restrict__ alpha,
+                                             const int *__restrict__ active, const SubGeom &g, int nvec)
 {
     typedef typename VRec<VP>::R R;
     constexpr int WB = wfmt_bytes(WF);
     constexpr int VBY = vfmt_bytes(VP);
     const int v0 = threadIdx.x * VB;  // nvec is a multiple of VB
-    // CTA tile of tlx * tly * tlz sites (threadIdx.y enumerates them, x'
-    // fastest); blockIdx.z covers (z'-tile, block).
-    const int pl = threadIdx.y % (tlx * tly);
-    const int xq = blockIdx.x * tlx + pl % tlx;
-    const int yq = blockIdx.y * tly + pl / tlx;
-    const int nzt = (g.hz + tlz - 1) / tlz;
-    const int blk = blockIdx.z / nzt;
-    const int zq = (blockIdx.z - blk * nzt) * tlz + threadIdx.y / (tlx * tly);
-    if (xq >= g.hx || yq >= g.hy || zq >= g.hz) return;
+    const int xq = blockIdx.x * blockDim.y + threadIdx.y;
+    if (xq >= g.hx) return;
     bool on[VB];
     bool any = false;
 #pragma unroll
@@ -171,6 +163,9 @@ __global__ void __launch_bounds__(512) k_step_il(const char *__restrict__ W, con
         any = any || on[k];
     }
     if (!any) return;
+    const int yq = blockIdx.y;
+    const int blk = blockIdx.z / g.hz;
+    const int zq = blockIdx.z - blk * g.hz;
     const int sy = g.hx, sz = g.hx * g.hy;
     const int i = zq * sz + yq * sy + xq;
     int fw[3], bw[3];
@@ -229,6 +224,24 @@ __global__ void __launch_bounds__(512) k_step_il(const char *__restrict__ W, con
         for (int k = 0; k < VB; ++k)
             if (on[k]) VRec<VP>::store(rout + (unsigned)i * rstride + k * VBY, o[k]);
     }
+}
+
+template <int VP, int WF, int VB, bool A16>
+__global__ void __launch_bounds__(256) k_step_il(const char *__restrict__ W, const char *__restrict__ in,
+                                                 char *__restrict__ out, const double *__restrict__ alpha,
+                                                 const int *__restrict__ active, SubGeom g, int nvec)
+{
+    step_il_body<VP, WF, VB, A16>(W, in, out, alpha, active, g, nvec);
+}
+
+// The same kernel held to 64 registers (CTAs of at most 128 threads, 8 per
+// SM): more warps in flight for the latency of the neighbour loads.
+template <int VP, int WF, int VB, bool A16>
+__global__ void __launch_bounds__(128, 8) k_step_il_occ(const char *__restrict__ W, const char *__restrict__ in,
+                                                        char *__restrict__ out, const double *__restrict__ alpha,
+                                                        const int *__restrict__ active, SubGeom g, int nvec)
+{
+    step_il_body<VP, WF, VB, A16>(W, in, out, alpha, active, g, nvec);
 }
 
 // --------------------------------------------------------------------------
@@ -493,21 +506,21 @@ inline int il_spb(int nvec, int threads)
 template <int VP, int WF, int VB, bool A16> cudaError_t step_il_launch(const StepArgs &a)
 {
     const int tx = a.nvec / VB;
-    int t0 = a.tile[0], t1 = a.tile[1], t2 = a.tile[2];
-    if (t0 <= 0 || t1 <= 0 || t2 <= 0) {  // default: a strip of sites along x'
-        t0 = il_spb(tx, a.threads);
-        t1 = t2 = 1;
-    }
-    t0 = std::min(t0, a.g.hx);
-    t1 = std::min(t1, a.g.hy);
-    t2 = std::min(t2, a.g.hz);
-    if (tx * t0 * t1 * t2 > 512) return cudaErrorInvalidConfiguration;
-    dim3 block(tx, t0 * t1 * t2);
-    const unsigned nzt = (unsigned)((a.g.hz + t2 - 1) / t2);
-    dim3 grid((a.g.hx + t0 - 1) / t0, (a.g.hy + t1 - 1) / t1, nzt * (unsigned)a.nblk);
+    // a strip of spb consecutive x' per CTA; tile[0] > 0 sets spb explicitly
+    // threads = -128 selects the 64-register variant (CTAs of <= 128 threads)
+    const bool occ = a.threads < 0;
+    const int cap = occ ? 128 : 256;
+    int spb = a.tile[0] > 0 ? a.tile[0] : il_spb(tx, occ ? 128 : a.threads);
+    spb = std::max(1, std::min(spb, cap / tx));
+    if (tx * spb > cap) return cudaErrorInvalidConfiguration;
+    dim3 block(tx, spb);
+    dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    k_step_il<VP, WF, VB, A16><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g, a.nvec, t0,
-                                                             t1, t2);
+    if (occ)
+        k_step_il_occ<VP, WF, VB, A16><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g,
+                                                                     a.nvec);
+    else
+        k_step_il<VP, WF, VB, A16><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g, a.nvec);
     return cudaGetLastError();
 }
 

@@ -55,6 +55,8 @@ cudaError_t launch_step(const StepArgs &a);
 cudaError_t launch_step_il(const StepArgs &a);
 // The same step marching along z' with a register window (interleaved layout, active unused).
 cudaError_t launch_step_zm(const StepArgs &a);
+// One-link Gaussian smearing step psi + alpha H psi (interleaved layout; W = the link field).
+cudaError_t launch_hop(const StepArgs &a);
 // The same step with TMA row staging in shared memory (k_rows.cuh); err gets
 // DERR_TIMEOUT if a bounded wait runs out.  rows_applicable says whether the
 // shape and formats allow it (16-byte bulk copies, CTA size, shared memory).
@@ -74,6 +76,10 @@ cudaError_t launch_step_il_f32(const StepArgs &a);
 cudaError_t launch_step_il_f16(const StepArgs &a);
 cudaError_t launch_step_il_bf16(const StepArgs &a);
 cudaError_t launch_step_zm_f64(const StepArgs &a);
+cudaError_t launch_hop_f64(const StepArgs &a);
+cudaError_t launch_hop_f32(const StepArgs &a);
+cudaError_t launch_hop_f16(const StepArgs &a);
+cudaError_t launch_hop_bf16(const StepArgs &a);
 cudaError_t launch_step_zm_f32(const StepArgs &a);
 cudaError_t launch_step_zm_f16(const StepArgs &a);
 cudaError_t launch_step_zm_bf16(const StepArgs &a);
@@ -96,6 +102,8 @@ cudaError_t launch_ingest_gauge(const double *U, int nd, double *Up, const SubGe
 cudaError_t launch_export_gauge(const double *Up, double *out, const SubGeom &g, const int L[4], cudaStream_t s);
 cudaError_t launch_build_twolink(const double *Up, char *W, int wfmt, const SubGeom &g, int nblk, int *err,
                                  cudaStream_t s);
+// The one-link field: U itself rounded into a W format (same planes as W).
+cudaError_t launch_build_links(const double *Up, char *L1, int wfmt, const SubGeom &g, int nblk, cudaStream_t s);
 cudaError_t launch_export_twolink(const char *W, int wfmt, double *out, const SubGeom &g, const int L[4],
                                   cudaStream_t s);
 // Whether the interleaved pack/unpack use the row transposes (contiguous canonical rows).

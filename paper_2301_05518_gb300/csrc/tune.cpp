@@ -33,12 +33,7 @@ std::vector<Cand> candidates(int nvec, int storage, bool rows)
         const int tx = G / vb;
         for (int t : {64, 128, 256})
             if (t >= tx || t == 256) c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 0, 0}});
-        // 3-D site tiles: more of each site's neighbours are records this CTA reads anyway
-        static const int tiles[][3] = {{2, 2, 2}, {4, 2, 2}, {4, 4, 1}, {4, 4, 2}, {8, 2, 2}, {2, 4, 4}};
-        for (const auto &tl : tiles) {
-            const int sites = tl[0] * tl[1] * tl[2];
-            if (tx * sites <= 512 && tx * sites >= 64) c.push_back({TLS_KERNEL_MRHS, vb, 0, {tl[0], tl[1], tl[2]}});
-        }
+        if (tx <= 128) c.push_back({TLS_KERNEL_MRHS, vb, -128, {0, 0, 0}});
         if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0, {0, 0, 0}});
     }
     const int vmax = storage == TLS_F64 ? 4 : 8;

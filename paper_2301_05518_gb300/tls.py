@@ -47,7 +47,7 @@ EXPORTS = (
     "tls_create", "tls_destroy", "tls_last_error", "tls_version", "tls_bytes_in_use",
     "tls_load_gauge", "tls_build_twolink", "tls_free_gauge", "tls_export_twolink",
     "tls_export_gauge", "tls_smear", "tls_set_profiling", "tls_get_profile",
-    "tls_smear_noalloc", "tls_set_barrier_budget", "tls_autotune", "tls_tune_set", "tls_serve_start", "tls_serve_stop", "tls_serve_submit",
+    "tls_smear_noalloc", "tls_build_links", "tls_smear_onelink", "tls_set_barrier_budget", "tls_autotune", "tls_tune_set", "tls_serve_start", "tls_serve_stop", "tls_serve_submit",
     "tls_serve_poll", "tls_serve_wait",
 )
 
@@ -104,6 +104,8 @@ def _load() -> ctypes.CDLL:
         "tls_export_gauge": ([P, I64, P, I, P], I),
         "tls_smear": ([P, I64, P, I, I, I, I, D, I, I, I, P, P], I),
         "tls_smear_noalloc": ([P, I64, P, I, I, I, D, I, I, P], I),
+        "tls_build_links": ([P, I64, I, I, P], I),
+        "tls_smear_onelink": ([P, I64, P, I, I, I, I, D, I, I, P, P], I),
         "tls_set_profiling": ([P, I], I),
         "tls_get_profile": ([P, ctypes.POINTER(tls_profile)], I),
         "tls_set_barrier_budget": ([P, I64], I),
@@ -218,6 +220,21 @@ def tls_smear(ctx, gauge: int, vecs, io_prec: int, nvec: int, N: int, width: flo
     nptr = ctypes.c_void_p(nout.ctypes.data) if norms else None
     _check(lib.tls_smear(ctx, int(gauge), p, int(io_prec), on_dev, int(nvec), int(N), float(width),
                          int(timeslice), int(storage), int(kernel), _stream(stream), nptr))
+    return nout
+
+
+def tls_build_links(ctx, gauge: int, prec: int = TLS_F32, keep_U: int = 1, stream=None) -> None:
+    _check(lib.tls_build_links(ctx, int(gauge), int(prec), int(keep_U), _stream(stream)))
+
+
+def tls_smear_onelink(ctx, gauge: int, vecs, io_prec: int, nvec: int, N: int, alpha: float,
+                      timeslice: int = TLS_ALL_T, storage: int = TLS_F32, stream=None, norms: bool = False):
+    """One-link Gaussian smearing (1 + alpha H)^N (Eq. 3, C = 1), in place."""
+    p, on_dev = _ptr(vecs)
+    nout = np.zeros(int(nvec), dtype=np.float64) if norms else None
+    nptr = ctypes.c_void_p(nout.ctypes.data) if norms else None
+    _check(lib.tls_smear_onelink(ctx, int(gauge), p, int(io_prec), on_dev, int(nvec), int(N), float(alpha),
+                                 int(timeslice), int(storage), _stream(stream), nptr))
     return nout
 
 
@@ -338,6 +355,13 @@ class Context:
               kernel=TLS_KERNEL_AUTO, stream=None, norms=False):
         return tls_smear(self.h, gauge, vecs, io_prec, nvec, N, width, timeslice, storage, kernel,
                          stream, norms)
+
+    def build_links(self, gauge, prec=TLS_F32, keep_U=1, stream=None):
+        return tls_build_links(self.h, gauge, prec, keep_U, stream)
+
+    def smear_onelink(self, gauge, vecs, io_prec, nvec, N, alpha, timeslice=TLS_ALL_T, storage=TLS_F32,
+                      stream=None, norms=False):
+        return tls_smear_onelink(self.h, gauge, vecs, io_prec, nvec, N, alpha, timeslice, storage, stream, norms)
 
     def smear_noalloc(self, gauge, vecs, io_prec, nvec, N, width, timeslice=TLS_ALL_T, storage=TLS_F32,
                       stream=None):

@@ -420,9 +420,9 @@ def test_rows_kernel_at_headline_shape_sampled(ctx, T):
         assert rel_l2(vecs[v, 1:2].cpu().numpy().astype(np.complex128), want) <= 2e-6 * 8
 
 
-@pytest.mark.parametrize("tile,vb", [((2, 2, 2), 2), ((4, 4, 2), 1), ((8, 2, 2), 4), ((3, 5, 2), 2)])
-def test_interleaved_tiles_bitwise_equal_single(ctx, T, tile, vb):
-    """3-D CTA tiles of the multi-RHS kernel, including tiles that do not divide the sublattice."""
+@pytest.mark.parametrize("tile,vb", [((2, 0, 0), 2), ((5, 0, 0), 1), ((8, 0, 0), 4), ((3, 0, 0), 2)])
+def test_interleaved_strips_bitwise_equal_single(ctx, T, tile, vb):
+    """Explicit strip lengths of the multi-RHS kernel, including ones that do not divide hx."""
     dims = (12, 10, 8, 2)
     nvec = 8
     U = gauge(dims, "haar", 35)
@@ -436,3 +436,40 @@ def test_interleaved_tiles_bitwise_equal_single(ctx, T, tile, vb):
     ctx.smear(gid, b, T.TLS_F32, nvec, 6, 1.3, storage=T.TLS_F32, kernel=T.TLS_KERNEL_SINGLE)
     ctx.free_gauge(gid)
     assert torch.equal(a, b)
+
+
+# ------------------------------------------------------------------ one-link Gaussian smearing (Eq. 2-3)
+@pytest.mark.parametrize("storage,nvec,t0,dims", [("F64", 3, -1, (6, 4, 8, 3)), ("F32", 4, 1, (8, 8, 4, 2)),
+                                                  ("F32", 5, -1, (2, 6, 4, 2)), ("F16", 6, -1, (8, 4, 6, 2)),
+                                                  ("BF16", 2, 0, (4, 4, 4, 1))])
+def test_onelink_smear_matches_oracle(ctx, T, storage, nvec, t0, dims):
+    U = gauge(dims, "haar", 41)
+    vecs = synth.gaussian_vectors(dims, nvec, 42)
+    N, alpha = 6, 0.09
+    want = oracle.smear_onelink(U.numpy(), vecs.numpy(), N, alpha, t0=t0)
+    st = getattr(T, "TLS_" + storage)
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.build_links(gid, T.TLS_F64 if st == T.TLS_F64 else T.TLS_F32)
+    x = vecs.to(torch.complex128 if st == T.TLS_F64 else torch.complex64).cuda()
+    norms = ctx.smear_onelink(gid, x, T.TLS_F64 if st == T.TLS_F64 else T.TLS_F32, nvec, N, alpha, timeslice=t0,
+                              storage=st, norms=True)
+    ctx.free_gauge(gid)
+    got = x.cpu().numpy().astype(np.complex128)
+    errs = per_vector_rel_l2(got, want)
+    assert max(errs) <= tol(st, N), errs
+    sl = slice(None) if t0 < 0 else slice(t0, t0 + 1)
+    assert np.allclose(norms, (np.abs(got[:, sl]) ** 2).reshape(nvec, -1).sum(1), rtol=1e-12, atol=0)
+
+
+def test_onelink_needs_links(ctx, T):
+    dims = (4, 4, 4, 1)
+    gid = ctx.load_gauge(gauge(dims, "haar", 43), 4, dims)
+    x = synth.gaussian_vectors(dims, 1, 44, dtype=torch.complex64).cuda()
+    with pytest.raises(T.TLSError) as e:
+        ctx.smear_onelink(gid, x, T.TLS_F32, 1, 3, 0.1)
+    assert e.value.status == T.TLS_ERR_NOT_BUILT
+    ctx.build_links(gid, T.TLS_F32)
+    with pytest.raises(T.TLSError) as e:
+        ctx.smear_onelink(gid, x.to(torch.complex128), T.TLS_F64, 1, 3, 0.1, storage=T.TLS_F64)
+    assert e.value.status == T.TLS_ERR_UNSUPPORTED
+    ctx.free_gauge(gid)

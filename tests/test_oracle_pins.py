@@ -332,3 +332,84 @@ def test_generator_reproducible_by_slice():
     U = synth.gauge_near_unit(dims, 0.2, 5)
     U1 = synth.gauge_near_unit((4, 4, 4, 1), 0.2, 5)
     assert torch.equal(U[0], U1[0])
+
+
+
+# --------------------------------------------------------------------------- one-link (Eq. 2-4)
+@pytest.mark.parametrize("dims,n,alpha", [((8, 8, 8, 2), 6, 0.1), ((6, 10, 4, 1), 4, -0.05)])
+def test_onelink_free_field_fourier(dims, n, alpha):
+    """U = 1: a plane wave picks up (1 + alpha sum_mu 2 cos k_mu)^n."""
+    U = _gauge(dims, 0, "unit")
+    psi = _gauss(dims, 1, 91)[0]
+    got = oracle.smear_onelink(U, psi, n, alpha)
+    Lt, Lz, Ly, Lx, _ = psi.shape
+    kz = 2 * np.pi * np.arange(Lz) / Lz
+    ky = 2 * np.pi * np.arange(Ly) / Ly
+    kx = 2 * np.pi * np.arange(Lx) / Lx
+    c = (2 * np.cos(kz)[:, None, None] + 2 * np.cos(ky)[None, :, None] + 2 * np.cos(kx)[None, None, :])
+    want = np.fft.ifftn(np.fft.fftn(psi, axes=(1, 2, 3)) * ((1 + alpha * c) ** n)[None, :, :, :, None],
+                        axes=(1, 2, 3))
+    assert rel_l2(got, want) < 1e-13
+
+
+def test_onelink_hermitian_and_covariant():
+    dims = (4, 6, 4, 2)
+    U = _gauge(dims, 92, "haar", nd=3)
+    phi, psi = _gauss(dims, 2, 93)
+    hphi, hpsi = oracle.apply_hop(U, phi), oracle.apply_hop(U, psi)
+    assert abs(np.vdot(phi, hpsi) - np.vdot(hphi, psi)) < 1e-14 * np.linalg.norm(phi) * np.linalg.norm(hpsi)
+    G = synth.gauge_transform_haar(dims, 94).numpy()
+    Ug = np.empty_like(U)
+    for i, ax in enumerate((3, 2, 1)):
+        Ug[..., i, :, :] = G @ U[..., i, :, :] @ np.conj(np.swapaxes(np.roll(G, -1, axis=ax), -1, -2))
+    a = oracle.smear_onelink(Ug, np.einsum("...ij,...j->...i", G, psi), 5, 0.12)
+    b = np.einsum("...ij,...j->...i", G, oracle.smear_onelink(U, psi, 5, 0.12))
+    assert rel_l2(a, b) < 1e-13
+
+
+def test_onelink_laplacian_rewrite():
+    """Sec. 2: C(1 + alpha H)^n = C' (1 + alpha' Lap)^n, C' = C(1+6 alpha)^n, alpha' = alpha/(1+6 alpha).
+
+    The right side is built from the one-link Laplacian Lap = H - 6 applied step by step.
+    """
+    dims = (4, 4, 6, 1)
+    U = _gauge(dims, 95, "near")
+    psi = _gauss(dims, 1, 96)[0]
+    n, alpha = 5, 0.08
+    lhs = oracle.smear_onelink(U, psi, n, alpha)
+    ap = alpha / (1 + 6 * alpha)
+    x = psi.copy()
+    for _ in range(n):
+        x = x + ap * (oracle.apply_hop(U, x) - 6 * x)
+    assert rel_l2(lhs, (1 + 6 * alpha) ** n * x) < 1e-13
+
+
+def test_twolink_is_the_straight_part_of_h_squared():
+    """Sec. 2: the two-link hops are the straight two-step paths of the one-link hops.
+
+    Each single hop (one direction, one sign) is written out here with numpy
+    (roll + einsum).  Applying the same hop twice and summing over the six
+    (direction, sign) pairs gives the straight +-2 mu paths, which must equal the
+    oracle's (Delta + 6) psi (Eq. tlLapl1 / Eq. tlLapl2).  The sum of the six
+    single hops must equal the oracle's H psi (Eq. 2).
+    """
+    dims = (6, 6, 6, 1)
+    U = _gauge(dims, 97, "haar", nd=3)
+    psi = _gauss(dims, 1, 98)[0]
+    W = oracle.twolink(U)
+    two = oracle.apply_lap(W, psi) + 6 * psi
+    # straight two-step paths from single hops: forward-forward and backward-backward per direction
+    def hop_dir(vec, mu, sign):
+        out = np.zeros_like(vec)
+        ax = (3, 2, 1)[mu]
+        if sign > 0:
+            out = np.einsum("...ij,...j->...i", U[..., mu, :, :], np.roll(vec, -1, axis=ax))
+        else:
+            Um = np.roll(U[..., mu, :, :], 1, axis=ax)
+            out = np.einsum("...ji,...j->...i", np.conj(Um), np.roll(vec, 1, axis=ax))
+        return out
+    straight = sum(hop_dir(hop_dir(psi, mu, s), mu, s) for mu in range(3) for s in (1, -1))
+    assert rel_l2(two, straight) < 1e-14
+    # and the full one-link H is the sum of the six single hops
+    h = sum(hop_dir(psi, mu, s) for mu in range(3) for s in (1, -1))
+    assert rel_l2(oracle.apply_hop(U, psi), h) < 1e-14
