@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--small", action="store_true", help="16^3x8 lattice, for quick checks only")
     ap.add_argument("--lattice", default=None, help="Lx,Ly,Lz,Lt override (profiling cases)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (planner default)")
+    ap.add_argument("--vb", type=int, default=0, help="with --kernel: vectors per thread (profiling cases)")
+    ap.add_argument("--threads", type=int, default=0, help="with --kernel: threads per CTA (profiling cases)")
+    ap.add_argument("--tile", default="0,0,0", help="with --kernel: tile entry of the tune table")
     ap.add_argument("--serving", action="store_true", help="run only the serving benchmark (longer)")
     ap.add_argument("--serve-jobs", type=int, default=60, help="open-loop jobs of the serving run")
     ap.add_argument("--no-extra", action="store_true", help="skip e2e, cpu baseline and side measurements")
@@ -369,6 +372,12 @@ def our_arm(args):
     launches_per_step = [0]
     prof_last = {}
     tune = None
+    if kernel != T.TLS_KERNEL_AUTO and (args.vb or args.threads or args.tile != "0,0,0"):
+        gid = ctx.load_gauge(U, 4, dims, stream=stream)
+        ctx.build_twolink(gid, wprec, T.TLS_R18, keep_U=0, stream=stream)
+        ctx.tune_set(gid, nvec, storage, T.TLS_ALL_T, kernel, args.vb, args.threads,
+                     tuple(int(x) for x in args.tile.split(",")))
+        ctx.free_gauge(gid)
     if kernel == T.TLS_KERNEL_AUTO and not args.no_tune:
         gid = ctx.load_gauge(U, 4, dims, stream=stream)
         ctx.build_twolink(gid, wprec, T.TLS_R18, keep_U=0, stream=stream)

@@ -247,7 +247,11 @@ typedef struct {
     int vecs_per_thread;    /* vectors per thread (planar kernels)             */
     int threads;            /* threads per CTA                                 */
     int tile[3];            /* multi-RHS kernel: tile[0] > 0 sets the sites    */
-                            /* per CTA (a strip along x'); tile[1..2] unused   */
+                            /* per CTA (a strip along x'); persistent kernel:  */
+                            /* tile[0] > 0 sets the L2 budget of one group of  */
+                            /* blocks in MB (default 48); multi-RHS kernel:    */
+                            /* tile[1] > 0 stages the strip's W in shared      */
+                            /* memory; tile[2] unused                          */
     double ms_per_step;     /* measured time of one smearing step              */
 } tls_tune_entry;
 

@@ -679,7 +679,8 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         if (occ <= 0) return fail(TLS_ERR_UNSUPPORTED, "tls_smear: persistent kernel cannot be resident");
         const int SBY = vfmt_bytes(sprec);
         const double per_blk = (double)g.Ps * (3.0 * wfmt_bytes(fmt) + 2.0 * nvec * SBY);
-        const double budget = 48.0 * (1 << 20);
+        // L2 budget of one group: tile[0] MB from the tune table, else 48 MB
+        const double budget = (tile[0] > 0 ? tile[0] : 48) * double(1 << 20);
         int gb = (int)std::max(1.0, std::floor(budget / per_blk));
         const int64_t want_items = (int64_t)occ * ctx->num_sms * threads;
         const int nchunk = (nvec + vb - 1) / vb;

@@ -245,6 +245,116 @@ __global__ void __launch_bounds__(128, 8) k_step_il_occ(const char *__restrict__
 }
 
 // --------------------------------------------------------------------------
+// Interleaved multi-RHS step with the strip's W staged in shared memory.
+// The CTA's spb sites need six W matrices each (W_d(x) and W_d(x - 2d) for
+// d = x, y, z).  They are copied once per CTA into shared memory, in the same
+// plane layout with plane stride spb, and every thread of a site reads them
+// from there: one cooperative copy instead of 30 global loads per thread.
+// Same FMA sequence as site_step.
+// --------------------------------------------------------------------------
+template <int VP, int WF, int VB, bool A16>
+__global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, const char *__restrict__ in,
+                                                  char *__restrict__ out, const double *__restrict__ alpha,
+                                                  SubGeom g, int nvec)
+{
+    typedef typename VRec<VP>::R R;
+    constexpr int WB = wfmt_bytes(WF);
+    constexpr int VBY = vfmt_bytes(VP);
+    constexpr int NQ = WB / 16, REM = WB % 16;
+    extern __shared__ __align__(16) unsigned char wsm[];
+    const int spb = blockDim.y;
+    const int x0 = blockIdx.x * spb;
+    const int yq = blockIdx.y;
+    const int blk = blockIdx.z / g.hz;
+    const int zq = blockIdx.z - blk * g.hz;
+    const int sy = g.hx, sz = g.hx * g.hy;
+    const int row = zq * sz + yq * sy;
+    const int ym = yq == 0 ? g.hy - 1 : yq - 1;
+    const int zm = zq == 0 ? g.hz - 1 : zq - 1;
+    const char *wb = W + (int64_t)blk * 3 * g.Ps * WB;
+    const int nsite = min(spb, g.hx - x0);
+    // set q = 0..5: (fwd x, bwd x, fwd y, bwd y, fwd z, bwd z), site k -> global site
+    auto gsite = [&](int q, int k) {
+        const int xq = x0 + k;
+        switch (q) {
+        case 1: return row + (xq == 0 ? g.hx - 1 : xq - 1);
+        case 3: return zq * sz + ym * sy + xq;
+        case 5: return zm * sz + yq * sy + xq;
+        default: return row + xq;
+        }
+    };
+    const int setB = (spb * WB + 15) / 16 * 16;  // one set: planes of spb words, 16-byte aligned
+    {
+        const int words = NQ + (REM ? 1 : 0);
+        const int total = 6 * nsite * words;
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        for (int e = tid; e < total; e += blockDim.x * blockDim.y) {
+            const int j = e % words;
+            const int k = (e / words) % nsite;
+            const int q = e / (words * nsite);
+            const int d = q >> 1;
+            const char *src = wb + (int64_t)d * g.Ps * WB;
+            char *dst = reinterpret_cast<char *>(wsm) + q * setB;
+            const int gi = gsite(q, k);
+            if (j < NQ)
+                reinterpret_cast<uint4 *>(dst)[j * spb + k] = reinterpret_cast<const uint4 *>(src)[(int64_t)j * g.Ps + gi];
+            else if (REM == 8)
+                reinterpret_cast<uint2 *>(dst + NQ * spb * 16)[k] =
+                    reinterpret_cast<const uint2 *>(src + (int64_t)NQ * g.Ps * 16)[gi];
+            else
+                reinterpret_cast<uint32_t *>(dst + NQ * spb * 16)[k] =
+                    reinterpret_cast<const uint32_t *>(src + (int64_t)NQ * g.Ps * 16)[gi];
+        }
+    }
+    __syncthreads();
+    const int k = threadIdx.y;
+    if (k >= nsite) return;
+    const int v0 = threadIdx.x * VB;
+    const int xq = x0 + k;
+    const int i = row + xq;
+    int fw[3], bw[3];
+    fw[0] = xq == g.hx - 1 ? i - (g.hx - 1) : i + 1;
+    bw[0] = xq == 0 ? i + (g.hx - 1) : i - 1;
+    fw[1] = yq == g.hy - 1 ? i - (g.hy - 1) * sy : i + sy;
+    bw[1] = yq == 0 ? i + (g.hy - 1) * sy : i - sy;
+    fw[2] = zq == g.hz - 1 ? i - (g.hz - 1) * sz : i + sz;
+    bw[2] = zq == 0 ? i + (g.hz - 1) * sz : i - sz;
+    const char *rin = in + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
+    char *rout = out + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
+    const unsigned rstride = (unsigned)nvec * VBY;
+    const char *ws = reinterpret_cast<const char *>(wsm);
+    cpx<R> acc[VB][3];
+#pragma unroll
+    for (int kk = 0; kk < VB; ++kk)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[kk][c].re = acc[kk][c].im = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        cpx<R> m[9], p[VB][3];
+        WFmt<WF>::load(ws + (2 * d) * setB, spb, k, m);
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)fw[d] * rstride, p);
+#pragma unroll
+        for (int kk = 0; kk < VB; ++kk) mv_add(m, p[kk], acc[kk]);
+        WFmt<WF>::load(ws + (2 * d + 1) * setB, spb, k, m);
+        RecGroup<VP, VB, A16>::load(rin + (unsigned)bw[d] * rstride, p);
+#pragma unroll
+        for (int kk = 0; kk < VB; ++kk) mdv_add(m, p[kk], acc[kk]);
+    }
+    cpx<R> c[VB][3], o[VB][3];
+    RecGroup<VP, VB, A16>::load(rin + (unsigned)i * rstride, c);
+#pragma unroll
+    for (int kk = 0; kk < VB; ++kk) {
+        const R a = (R)alpha[v0 + kk];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            o[kk][q].re = fma(a, fma(R(-6), c[kk][q].re, acc[kk][q].re), c[kk][q].re);
+            o[kk][q].im = fma(a, fma(R(-6), c[kk][q].im, acc[kk][q].im), c[kk][q].im);
+        }
+    }
+    RecGroup<VP, VB, A16>::store(rout + (unsigned)i * rstride, o);
+}
+
+// --------------------------------------------------------------------------
 // Multi-RHS step on the interleaved layout, marching along z'.
 // CTA = (nvec/VB, spb): threadIdx.x picks VB adjacent vectors, threadIdx.y
 // one of spb consecutive x' of row y' = blockIdx.y in block blockIdx.z; each
@@ -516,7 +626,10 @@ template <int VP, int WF, int VB, bool A16> cudaError_t step_il_launch(const Ste
     dim3 block(tx, spb);
     dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    if (occ)
+    if (a.tile[1] > 0 && a.active == nullptr)  // W of the strip staged in shared memory
+        k_step_ilw<VP, WF, VB, A16><<<grid, block, 6 * ((spb * wfmt_bytes(WF) + 15) / 16 * 16), a.stream>>>(
+            a.W, a.in, a.out, a.alpha, a.g, a.nvec);
+    else if (occ)
         k_step_il_occ<VP, WF, VB, A16><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g,
                                                                      a.nvec);
     else

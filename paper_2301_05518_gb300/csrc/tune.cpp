@@ -34,11 +34,15 @@ std::vector<Cand> candidates(int nvec, int storage, bool rows)
         for (int t : {64, 128, 256})
             if (t >= tx || t == 256) c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 0, 0}});
         if (tx <= 128) c.push_back({TLS_KERNEL_MRHS, vb, -128, {0, 0, 0}});
+        for (int t : {128, 256})  // W of the strip staged in shared memory
+            if (t >= tx) c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 1, 0}});
         if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0, {0, 0, 0}});
     }
     const int vmax = storage == TLS_F64 ? 4 : 8;
     for (int vb : {1, 4, 8})
-        if (vb <= vmax && (vb == 1 || vb <= 2 * nvec)) c.push_back({TLS_KERNEL_PERSISTENT, vb, 256, {0, 0, 0}});
+        if (vb <= vmax && (vb == 1 || vb <= 2 * nvec))
+            for (int mb : {48, 96})  // L2 budget of one group of blocks (MB)
+                c.push_back({TLS_KERNEL_PERSISTENT, vb, 256, {mb, 0, 0}});
     return c;
 }
 

@@ -420,7 +420,8 @@ def test_rows_kernel_at_headline_shape_sampled(ctx, T):
         assert rel_l2(vecs[v, 1:2].cpu().numpy().astype(np.complex128), want) <= 2e-6 * 8
 
 
-@pytest.mark.parametrize("tile,vb", [((2, 0, 0), 2), ((5, 0, 0), 1), ((8, 0, 0), 4), ((3, 0, 0), 2)])
+@pytest.mark.parametrize("tile,vb", [((2, 0, 0), 2), ((5, 0, 0), 1), ((8, 0, 0), 4), ((3, 0, 0), 2),
+                                     ((0, 1, 0), 2), ((5, 1, 0), 4), ((3, 1, 0), 1)])
 def test_interleaved_strips_bitwise_equal_single(ctx, T, tile, vb):
     """Explicit strip lengths of the multi-RHS kernel, including ones that do not divide hx."""
     dims = (12, 10, 8, 2)
