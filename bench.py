@@ -345,6 +345,26 @@ def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0):
     return out
 
 
+def sink_run(T, ctx, device, stream, hbm_peak):
+    """Sink smearing in the many-source pattern: 72 dense vectors, n = 30, one W."""
+    from paper_2301_05518_gb300 import synth, workloads
+    w = workloads.SINK_SMEAR
+    dims, nvec, N, sigma = w["dims"], w["nvec"], w["N"], w["sigma"]
+    U = synth.gauge_near_unit(dims, w["eps"], w["gauge_seed"], nd=4, device=device)
+    x = synth.gaussian_vectors(dims, nvec, w["vec_seed"], dtype=torch.complex64, device=device)
+    gid = ctx.load_gauge(U, 4, dims, stream=stream)
+    ctx.build_twolink(gid, T.TLS_F32, T.TLS_R18, keep_U=0, stream=stream)
+    del U
+    best, _ = ctx.autotune(gid, nvec, T.TLS_F32, T.TLS_ALL_T, steps=3)
+    ctx.smear(gid, x, T.TLS_F32, nvec, N, sigma, storage=T.TLS_F32, stream=stream)
+    p = ctx.get_profile()
+    ctx.free_gauge(gid)
+    del x
+    gbs = p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9
+    return {"workload": w["name"], "vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3),
+            "ms_per_step": p["ms_iter"] / N, "gbs": gbs, "frac": gbs / hbm_peak, "kernel": best}
+
+
 def our_arm(args):
     import torch
     ws, rank, local = dist_setup("nccl")
@@ -519,6 +539,8 @@ def our_arm(args):
                                                 "(twolink + smear), %.1f s" % (nvec, nsl, Lt, N, dt)}
     if not args.no_extra:
         del U, vecs
+        torch.cuda.empty_cache()
+        extra["sink_smear"] = sink_run(T, ctx, local, stream, hbm_peak)
         torch.cuda.empty_cache()
         extra["serving"] = serving_run(T, local, n_closed=24, n_open=args.serve_jobs, time_cap_s=25.0,
                                        fp64_cap_s=10.0)

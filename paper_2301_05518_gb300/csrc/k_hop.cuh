@@ -15,7 +15,7 @@
 
 namespace tls {
 
-template <int VP, int WF, int VB, bool A16>
+template <int VP, int WF, int VB>
 __global__ void __launch_bounds__(512) k_hop_il(const char *__restrict__ L1, const char *__restrict__ in,
                                                 char *__restrict__ out, const double *__restrict__ alpha,
                                                 SubGeom g, int nvec)
@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(512) k_hop_il(const char *__restrict__ L1, con
     typedef typename VRec<VP>::R R;
     constexpr int WB = wfmt_bytes(WF);
     constexpr int VBY = vfmt_bytes(VP);
-    const int v0 = threadIdx.x * VB;
+    const int t = threadIdx.x, T = nvec / VB;
     const int xq = blockIdx.x * blockDim.y + threadIdx.y;
     if (xq >= g.hx) return;
     const int yq = blockIdx.y;
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(512) k_hop_il(const char *__restrict__ L1, con
     fw[2] = zq == g.hz - 1 ? i - (g.hz - 1) * sz : i + sz;
     bw[2] = zq == 0 ? i + (g.hz - 1) * sz : i - sz;
     const unsigned rstride = (unsigned)nvec * VBY;
-    auto recs = [&](int b) { return in + ((int64_t)b * g.Ps * nvec + v0) * VBY; };
+    auto recs = [&](int b) { return in + (int64_t)b * g.Ps * nvec * VBY; };
     auto links = [&](int b, int d) { return L1 + ((int64_t)b * 3 + d) * g.Ps * WB; };
     cpx<R> acc[VB][3];
 #pragma unroll
@@ -55,36 +55,36 @@ __global__ void __launch_bounds__(512) k_hop_il(const char *__restrict__ L1, con
         const int i_b = odd ? i : bw[d];
         cpx<R> m[9], p[VB][3];
         WFmt<WF>::load(links(blk, d), g.Ps, i, m);
-        RecGroup<VP, VB, A16>::load(recs(nb) + (unsigned)i_f * rstride, p);
+        RecGroup<VP, VB>::load(recs(nb) + (unsigned)i_f * rstride, nvec, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
         WFmt<WF>::load(links(nb, d), g.Ps, i_b, m);
-        RecGroup<VP, VB, A16>::load(recs(nb) + (unsigned)i_b * rstride, p);
+        RecGroup<VP, VB>::load(recs(nb) + (unsigned)i_b * rstride, nvec, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
     }
     cpx<R> c[VB][3], o[VB][3];
-    RecGroup<VP, VB, A16>::load(recs(blk) + (unsigned)i * rstride, c);
+    RecGroup<VP, VB>::load(recs(blk) + (unsigned)i * rstride, nvec, t, T, c);
 #pragma unroll
     for (int k = 0; k < VB; ++k) {
-        const R a = (R)alpha[v0 + k];
+        const R a = (R)alpha[il_vec<VP, VB>(t, T, k)];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             o[k][q].re = fma(a, acc[k][q].re, c[k][q].re);
             o[k][q].im = fma(a, acc[k][q].im, c[k][q].im);
         }
     }
-    RecGroup<VP, VB, A16>::store(out + (((int64_t)blk * g.Ps + i) * nvec + v0) * VBY, o);
+    RecGroup<VP, VB>::store(out + ((int64_t)blk * g.Ps + i) * nvec * VBY, nvec, t, T, o);
 }
 
-template <int VP, int WF, int VB, bool A16> cudaError_t hop_launch(const StepArgs &a)
+template <int VP, int WF, int VB> cudaError_t hop_launch(const StepArgs &a)
 {
     const int tx = a.nvec / VB;
     const int spb = il_spb(tx, a.threads);
     dim3 block(tx, spb);
     dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    k_hop_il<VP, WF, VB, A16><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g, a.nvec);
+    k_hop_il<VP, WF, VB><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g, a.nvec);
     return cudaGetLastError();
 }
 
@@ -95,12 +95,8 @@ template <int VP> cudaError_t hop_dispatch(const StepArgs &a)
     if (a.wfmt != WF) return cudaErrorNotSupported;
     if (a.nvec < 1 || a.nvec > 256) return cudaErrorInvalidValue;
     const int vb = (a.vb == 2 && a.nvec % 2 == 0) ? 2 : 1;
-    if constexpr (VP == P_F32) {
-        if (vb == 2) return hop_launch<VP, WF, 2, true>(a);
-    } else {
-        if (vb == 2) return hop_launch<VP, WF, 2, false>(a);
-    }
-    return hop_launch<VP, WF, 1, false>(a);
+    if (vb == 2) return hop_launch<VP, WF, 2>(a);
+    return hop_launch<VP, WF, 1>(a);
 }
 
 }  // namespace tls

@@ -264,7 +264,7 @@ __global__ void k_pack_il(const IO *__restrict__ src, int64_t svs, char *__restr
         val[k].re = (R)p[2 * k];
         val[k].im = (R)p[2 * k + 1];
     }
-    VRec<VP>::store(dst + (((int64_t)b * g.Ps + i) * rec_n + rec_v0 + v) * vfmt_bytes(VP), val);
+    VRec<VP>::store(dst + ((int64_t)b * g.Ps + i) * rec_n * vfmt_bytes(VP), rec_n, rec_v0 + v, val);
 }
 
 template <typename IO, int VP>
@@ -281,7 +281,7 @@ __global__ void k_unpack_il(const char *__restrict__ src, IO *__restrict__ dst, 
     const int64_t site = (((int64_t)t * Lz + c.z) * Ly + c.y) * Lx + c.x;
     typedef typename VRec<VP>::R R;
     cpx<R> val[3];
-    VRec<VP>::load(src + (((int64_t)b * g.Ps + i) * rec_n + rec_v0 + v) * vfmt_bytes(VP), val);
+    VRec<VP>::load(src + ((int64_t)b * g.Ps + i) * rec_n * vfmt_bytes(VP), rec_n, rec_v0 + v, val);
     IO *p = dst + ((int64_t)v * dvs + site) * 6;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -345,7 +345,8 @@ __global__ void __launch_bounds__(256) k_unpack_rows(const char *__restrict__ sr
     for (int k = threadIdx.x; k < nvec * Lx; k += blockDim.x) {
         const int v = k / Lx, x = k - v * Lx;
         cpx<R> val[3];
-        VRec<VP>::load(reinterpret_cast<const char *>(smr) + (x & 1) * segB + ((x >> 1) * rec_n + rec_v0 + v) * VBY, val);
+        VRec<VP>::load(reinterpret_cast<const char *>(smr) + (x & 1) * segB + (x >> 1) * rec_n * VBY, rec_n, rec_v0 + v,
+                       val);
         IO *p = dst + ((int64_t)v * dvs + site0 + x) * 6;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -388,7 +389,8 @@ __global__ void __launch_bounds__(256) k_pack_rows(const IO *__restrict__ src, i
             val[c].re = (R)p[2 * c];
             val[c].im = (R)p[2 * c + 1];
         }
-        VRec<VP>::store(reinterpret_cast<char *>(smr) + (x & 1) * segB + ((x >> 1) * rec_n + rec_v0 + v) * VBY, val);
+        VRec<VP>::store(reinterpret_cast<char *>(smr) + (x & 1) * segB + (x >> 1) * rec_n * VBY, rec_n, rec_v0 + v,
+                        val);
     }
     __syncthreads();
     for (int par = 0; par < 2; ++par) {

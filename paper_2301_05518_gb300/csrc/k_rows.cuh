@@ -102,7 +102,7 @@ template <int VB> struct RowsBound {
     static constexpr int threads = VB == 1 ? 768 : VB == 2 ? 384 : 256;
 };
 
-template <int VP, int WF, int VB, bool A16>
+template <int VP, int WF, int VB>
 __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char *__restrict__ W, const char *__restrict__ in,
                                                    char *__restrict__ out, const double *__restrict__ alpha,
                                                    SubGeom g, int nvec, RowsPlan pl, int *err)
@@ -140,11 +140,11 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
     const int tid = threadIdx.x;
     const int xq = tid / tx;
     const int vg = tid - xq * tx;
-    const int v0 = vg * VB;
+    const int t = vg, T = tx;  // this thread's vectors: il_vec(t, T, k)
     const bool worker = xq < hx;
     R a_v[VB];  // alpha per vector, converted once (keeps FP64 out of the row loop)
 #pragma unroll
-    for (int k = 0; k < VB; ++k) a_v[k] = worker ? (R)alpha[v0 + k] : R(0);
+    for (int k = 0; k < VB; ++k) a_v[k] = worker ? (R)alpha[il_vec<VP, VB>(t, T, k)] : R(0);
 
     auto row_of = [&](int z, int y) { return (z * hy + y) * hx; };
     auto ring4 = [](int r) { return (r + 4) & 3; };
@@ -237,13 +237,12 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
             const char *Wym = Wc + (ring3(y - 1) * 3 + 1) * wS;
             const char *Wzm = Wz + (y & 1) * wS;
             const unsigned rs = (unsigned)recB;
-            const unsigned vo = (unsigned)v0 * VBY;
             // Operand addresses of the six hops, in the order of site_step:
             // x forward, x backward, y forward, y backward, z forward, z backward.
             const char *wsrc[6] = {Wrow, Wrow, Wrow + wS, Wym, Wrow + 2 * wS, Wzm};
             const int wsite[6] = {xq, xm, xq, xq, xq, xq};
-            const char *psrc[6] = {Yc + xp * rs + vo, Yc + xm * rs + vo, Yp + xq * rs + vo,
-                                   Ym + xq * rs + vo, Zp + xq * rs + vo, Zm + xq * rs + vo};
+            const char *psrc[6] = {Yc + xp * rs, Yc + xm * rs, Yp + xq * rs,
+                                   Ym + xq * rs, Zp + xq * rs, Zm + xq * rs};
             cpx<R> acc[VB][3];
 #pragma unroll
             for (int k = 0; k < VB; ++k)
@@ -252,12 +251,12 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
             // software pipeline: the operands of hop h+1 are loaded before hop h is applied
             cpx<R> m[2][9], p[2][VB][3];
             WFmt<WF>::load(wsrc[0], hx, wsite[0], m[0]);
-            RecGroup<VP, VB, A16>::load(psrc[0], p[0]);
+            RecGroup<VP, VB>::load(psrc[0], nvec, t, T, p[0]);
 #pragma unroll
             for (int h = 0; h < 6; ++h) {
                 if (h + 1 < 6) {
                     WFmt<WF>::load(wsrc[h + 1], hx, wsite[h + 1], m[(h + 1) & 1]);
-                    RecGroup<VP, VB, A16>::load(psrc[h + 1], p[(h + 1) & 1]);
+                    RecGroup<VP, VB>::load(psrc[h + 1], nvec, t, T, p[(h + 1) & 1]);
                 }
 #pragma unroll
                 for (int k = 0; k < VB; ++k) {
@@ -268,7 +267,7 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
                 }
             }
             cpx<R> c[VB][3], o[VB][3];
-            RecGroup<VP, VB, A16>::load(Yc + xq * rs + vo, c);
+            RecGroup<VP, VB>::load(Yc + xq * rs, nvec, t, T, c);
 #pragma unroll
             for (int k = 0; k < VB; ++k) {
                 const R a = a_v[k];
@@ -278,7 +277,7 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
                     o[k][q].im = fma(a, fma(R(-6), c[k][q].im, acc[k][q].im), c[k][q].im);
                 }
             }
-            RecGroup<VP, VB, A16>::store(outblk + ((int64_t)row_of(zq, y) + xq) * recB + vo, o);
+            RecGroup<VP, VB>::store(outblk + ((int64_t)row_of(zq, y) + xq) * recB, nvec, t, T, o);
                 }
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[y & 1]);
@@ -310,16 +309,16 @@ inline bool rows_ok(int wfmt, int prec, const SubGeom &g, int nvec, int vb, int 
     return p.total <= max_smem;
 }
 
-template <int VP, int WF, int VB, bool A16> cudaError_t rows_launch(const StepArgs &a, int *err)
+template <int VP, int WF, int VB> cudaError_t rows_launch(const StepArgs &a, int *err)
 {
     const RowsPlan pl = rows_plan(a.g.hx, a.nvec, vfmt_bytes(VP), wfmt_bytes(WF));
     // per launch: the attribute belongs to the current device
-    cudaError_t e = cudaFuncSetAttribute(k_step_rows<VP, WF, VB, A16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_step_rows<VP, WF, VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          pl.total);
     if (e != cudaSuccess) return e;
     const int threads = (a.g.hx * (a.nvec / VB) + 31) / 32 * 32;
     dim3 grid(a.g.hz, a.nblk);
-    k_step_rows<VP, WF, VB, A16><<<grid, threads, pl.total, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g, a.nvec, pl,
+    k_step_rows<VP, WF, VB><<<grid, threads, pl.total, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g, a.nvec, pl,
                                                                        err);
     return cudaGetLastError();
 }
@@ -332,17 +331,16 @@ template <int VP, int WF> cudaError_t rows_w(const StepArgs &a, int *err)
         int vb = a.vb > 0 ? a.vb : 1;
         if (a.nvec % vb != 0) vb = 1;
         if constexpr (VP == P_F32) {
-            const bool a16 = (a.nvec % 2 == 0);
             switch (vb) {
-            case 2: return a16 ? rows_launch<VP, WF, 2, true>(a, err) : rows_launch<VP, WF, 2, false>(a, err);
-            case 4: return a16 ? rows_launch<VP, WF, 4, true>(a, err) : rows_launch<VP, WF, 4, false>(a, err);
-            default: return rows_launch<VP, WF, 1, false>(a, err);
+            case 2: return rows_launch<VP, WF, 2>(a, err);
+            case 4: return rows_launch<VP, WF, 4>(a, err);
+            default: return rows_launch<VP, WF, 1>(a, err);
             }
         } else {
             switch (vb) {
-            case 2: return rows_launch<VP, WF, 2, false>(a, err);
-            case 4: return rows_launch<VP, WF, 4, false>(a, err);
-            default: return rows_launch<VP, WF, 1, false>(a, err);
+            case 2: return rows_launch<VP, WF, 2>(a, err);
+            case 4: return rows_launch<VP, WF, 4>(a, err);
+            default: return rows_launch<VP, WF, 1>(a, err);
             }
         }
     }

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) k_step(const char *__restrict__ W, const 
 // per vector is the same sequence as site_step, so results are bitwise equal
 // to the planar kernels.
 // --------------------------------------------------------------------------
-template <int VP, int WF, int VB, bool A16>
+template <int VP, int WF, int VB>
 __device__ __forceinline__ void step_il_body(const char *__restrict__ W, const char *__restrict__ in,
                                              char *__restrict__ out, const double *__restrict__ alpha,
                                              const int *__restrict__ active, const SubGeom &g, int nvec)
@@ -152,14 +152,14 @@ __device__ __forceinline__ void step_il_body(const char *__restrict__ W, const c
     typedef typename VRec<VP>::R R;
     constexpr int WB = wfmt_bytes(WF);
     constexpr int VBY = vfmt_bytes(VP);
-    const int v0 = threadIdx.x * VB;  // nvec is a multiple of VB
+    const int t = threadIdx.x, T = nvec / VB;  // nvec is a multiple of VB
     const int xq = blockIdx.x * blockDim.y + threadIdx.y;
     if (xq >= g.hx) return;
     bool on[VB];
     bool any = false;
 #pragma unroll
     for (int k = 0; k < VB; ++k) {
-        on[k] = active == nullptr || active[v0 + k] != 0;
+        on[k] = active == nullptr || active[il_vec<VP, VB>(t, T, k)] != 0;
         any = any || on[k];
     }
     if (!any) return;
@@ -176,9 +176,9 @@ __device__ __forceinline__ void step_il_body(const char *__restrict__ W, const c
     fw[2] = zq == g.hz - 1 ? i - (g.hz - 1) * sz : i + sz;
     bw[2] = zq == 0 ? i + (g.hz - 1) * sz : i - sz;
     const char *wb = W + (int64_t)blk * 3 * g.Ps * WB;
-    // records of this block, vectors v0.. of site s at rin + s * nvec * VBY
-    const char *rin = in + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
-    char *rout = out + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
+    // record group of site s of this block at rin + s * nvec * VBY
+    const char *rin = in + (int64_t)blk * g.Ps * nvec * VBY;
+    char *rout = out + (int64_t)blk * g.Ps * nvec * VBY;
     const unsigned rstride = (unsigned)nvec * VBY;
     cpx<R> acc[VB][3];
 #pragma unroll
@@ -189,19 +189,19 @@ __device__ __forceinline__ void step_il_body(const char *__restrict__ W, const c
     for (int d = 0; d < 3; ++d) {
         cpx<R> m[9], p[VB][3];
         WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, i, m);
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)fw[d] * rstride, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, nvec, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
         WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, bw[d], m);
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)bw[d] * rstride, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, nvec, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
     }
     cpx<R> c[VB][3], o[VB][3];
-    RecGroup<VP, VB, A16>::load(rin + (unsigned)i * rstride, c);
+    RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, nvec, t, T, c);
 #pragma unroll
     for (int k = 0; k < VB; ++k) {
-        const R a = (R)alpha[v0 + k];
+        const R a = (R)alpha[il_vec<VP, VB>(t, T, k)];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             o[k][q].re = fma(a, fma(R(-6), c[k][q].re, acc[k][q].re), c[k][q].re);
@@ -218,30 +218,30 @@ __device__ __forceinline__ void step_il_body(const char *__restrict__ W, const c
             for (int k = 0; k < VB; ++k) all = all && on[k];
             return all;
         }())) {
-        RecGroup<VP, VB, A16>::store(rout + (unsigned)i * rstride, o);
+        RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, nvec, t, T, o);
     } else {
 #pragma unroll
         for (int k = 0; k < VB; ++k)
-            if (on[k]) VRec<VP>::store(rout + (unsigned)i * rstride + k * VBY, o[k]);
+            if (on[k]) VRec<VP>::store(rout + (unsigned)i * rstride, nvec, il_vec<VP, VB>(t, T, k), o[k]);
     }
 }
 
-template <int VP, int WF, int VB, bool A16>
+template <int VP, int WF, int VB>
 __global__ void __launch_bounds__(256) k_step_il(const char *__restrict__ W, const char *__restrict__ in,
                                                  char *__restrict__ out, const double *__restrict__ alpha,
                                                  const int *__restrict__ active, SubGeom g, int nvec)
 {
-    step_il_body<VP, WF, VB, A16>(W, in, out, alpha, active, g, nvec);
+    step_il_body<VP, WF, VB>(W, in, out, alpha, active, g, nvec);
 }
 
 // The same kernel held to 64 registers (CTAs of at most 128 threads, 8 per
 // SM): more warps in flight for the latency of the neighbour loads.
-template <int VP, int WF, int VB, bool A16>
+template <int VP, int WF, int VB>
 __global__ void __launch_bounds__(128, 8) k_step_il_occ(const char *__restrict__ W, const char *__restrict__ in,
                                                         char *__restrict__ out, const double *__restrict__ alpha,
                                                         const int *__restrict__ active, SubGeom g, int nvec)
 {
-    step_il_body<VP, WF, VB, A16>(W, in, out, alpha, active, g, nvec);
+    step_il_body<VP, WF, VB>(W, in, out, alpha, active, g, nvec);
 }
 
 // --------------------------------------------------------------------------
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(128, 8) k_step_il_occ(const char *__restrict__
 // from there: one cooperative copy instead of 30 global loads per thread.
 // Same FMA sequence as site_step.
 // --------------------------------------------------------------------------
-template <int VP, int WF, int VB, bool A16>
+template <int VP, int WF, int VB>
 __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, const char *__restrict__ in,
                                                   char *__restrict__ out, const double *__restrict__ alpha,
                                                   SubGeom g, int nvec)
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
     __syncthreads();
     const int k = threadIdx.y;
     if (k >= nsite) return;
-    const int v0 = threadIdx.x * VB;
+    const int t = threadIdx.x, T = nvec / VB;
     const int xq = x0 + k;
     const int i = row + xq;
     int fw[3], bw[3];
@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
     bw[1] = yq == 0 ? i + (g.hy - 1) * sy : i - sy;
     fw[2] = zq == g.hz - 1 ? i - (g.hz - 1) * sz : i + sz;
     bw[2] = zq == 0 ? i + (g.hz - 1) * sz : i - sz;
-    const char *rin = in + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
-    char *rout = out + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
+    const char *rin = in + (int64_t)blk * g.Ps * nvec * VBY;
+    char *rout = out + (int64_t)blk * g.Ps * nvec * VBY;
     const unsigned rstride = (unsigned)nvec * VBY;
     const char *ws = reinterpret_cast<const char *>(wsm);
     cpx<R> acc[VB][3];
@@ -332,26 +332,26 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
     for (int d = 0; d < 3; ++d) {
         cpx<R> m[9], p[VB][3];
         WFmt<WF>::load(ws + (2 * d) * setB, spb, k, m);
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)fw[d] * rstride, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, nvec, t, T, p);
 #pragma unroll
         for (int kk = 0; kk < VB; ++kk) mv_add(m, p[kk], acc[kk]);
         WFmt<WF>::load(ws + (2 * d + 1) * setB, spb, k, m);
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)bw[d] * rstride, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, nvec, t, T, p);
 #pragma unroll
         for (int kk = 0; kk < VB; ++kk) mdv_add(m, p[kk], acc[kk]);
     }
     cpx<R> c[VB][3], o[VB][3];
-    RecGroup<VP, VB, A16>::load(rin + (unsigned)i * rstride, c);
+    RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, nvec, t, T, c);
 #pragma unroll
     for (int kk = 0; kk < VB; ++kk) {
-        const R a = (R)alpha[v0 + kk];
+        const R a = (R)alpha[il_vec<VP, VB>(t, T, kk)];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             o[kk][q].re = fma(a, fma(R(-6), c[kk][q].re, acc[kk][q].re), c[kk][q].re);
             o[kk][q].im = fma(a, fma(R(-6), c[kk][q].im, acc[kk][q].im), c[kk][q].im);
         }
     }
-    RecGroup<VP, VB, A16>::store(rout + (unsigned)i * rstride, o);
+    RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, nvec, t, T, o);
 }
 
 // --------------------------------------------------------------------------
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
 // psi(z+2)'s prefetch, the x and y neighbours and five W matrices are loaded.
 // Same per-vector FMA sequence as site_step (bitwise equal results).
 // --------------------------------------------------------------------------
-template <int VP, int WF, int VB, bool A16>
+template <int VP, int WF, int VB>
 __global__ void __launch_bounds__(256) k_step_zm(const char *__restrict__ W, const char *__restrict__ in,
                                                  char *__restrict__ out, const double *__restrict__ alpha,
                                                  SubGeom g, int nvec)
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(256) k_step_zm(const char *__restrict__ W, con
     typedef typename VRec<VP>::R R;
     constexpr int WB = wfmt_bytes(WF);
     constexpr int VBY = vfmt_bytes(VP);
-    const int v0 = threadIdx.x * VB;
+    const int t = threadIdx.x, T = nvec / VB;
     const int xq = blockIdx.x * blockDim.y + threadIdx.y;
     if (xq >= g.hx) return;
     const int yq = blockIdx.y;
@@ -382,25 +382,25 @@ __global__ void __launch_bounds__(256) k_step_zm(const char *__restrict__ W, con
     const int yp = yq == g.hy - 1 ? 0 : yq + 1;
     const int ym = yq == 0 ? g.hy - 1 : yq - 1;
     const char *wb = W + (int64_t)blk * 3 * g.Ps * WB;
-    const char *rin = in + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
-    char *rout = out + ((int64_t)blk * g.Ps * nvec + v0) * VBY;
+    const char *rin = in + (int64_t)blk * g.Ps * nvec * VBY;
+    char *rout = out + (int64_t)blk * g.Ps * nvec * VBY;
     const unsigned rstride = (unsigned)nvec * VBY;
     R a_v[VB];
 #pragma unroll
-    for (int k = 0; k < VB; ++k) a_v[k] = (R)alpha[v0 + k];
+    for (int k = 0; k < VB; ++k) a_v[k] = (R)alpha[il_vec<VP, VB>(t, T, k)];
     const int col = yq * sy + xq;       // site index at z' = 0
     auto site = [&](int z) { return z * sz + col; };
     // column state: psi(z-1), psi(z), psi(z+1) and W_z(z-1)
     cpx<R> pm[VB][3], pc[VB][3], pp[VB][3], wzm[9];
-    RecGroup<VP, VB, A16>::load(rin + (unsigned)site(hz - 1) * rstride, pm);
-    RecGroup<VP, VB, A16>::load(rin + (unsigned)site(0) * rstride, pc);
-    RecGroup<VP, VB, A16>::load(rin + (unsigned)site(1 % hz) * rstride, pp);
+    RecGroup<VP, VB>::load(rin + (unsigned)site(hz - 1) * rstride, nvec, t, T, pm);
+    RecGroup<VP, VB>::load(rin + (unsigned)site(0) * rstride, nvec, t, T, pc);
+    RecGroup<VP, VB>::load(rin + (unsigned)site(1 % hz) * rstride, nvec, t, T, pp);
     WFmt<WF>::load(wb + 2 * g.Ps * WB, g.Ps, site(hz - 1), wzm);
     for (int z = 0; z < hz; ++z) {
         const int i = site(z);
         const int zn = (z + 2) % hz;
         cpx<R> pn[VB][3];  // psi(z+2): next iteration's psi(z+1)
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)site(zn) * rstride, pn);
+        RecGroup<VP, VB>::load(rin + (unsigned)site(zn) * rstride, nvec, t, T, pn);
         cpx<R> acc[VB][3];
 #pragma unroll
         for (int k = 0; k < VB; ++k)
@@ -409,20 +409,20 @@ __global__ void __launch_bounds__(256) k_step_zm(const char *__restrict__ W, con
         cpx<R> m[9], p[VB][3], wz[9];
         // x forward / backward
         WFmt<WF>::load(wb, g.Ps, i, m);
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)(i - xq + xp) * rstride, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)(i - xq + xp) * rstride, nvec, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
         WFmt<WF>::load(wb, g.Ps, i - xq + xm, m);
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)(i - xq + xm) * rstride, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)(i - xq + xm) * rstride, nvec, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
         // y forward / backward
         WFmt<WF>::load(wb + g.Ps * WB, g.Ps, i, m);
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)(i + (yp - yq) * sy) * rstride, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)(i + (yp - yq) * sy) * rstride, nvec, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
         WFmt<WF>::load(wb + g.Ps * WB, g.Ps, i + (ym - yq) * sy, m);
-        RecGroup<VP, VB, A16>::load(rin + (unsigned)(i + (ym - yq) * sy) * rstride, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)(i + (ym - yq) * sy) * rstride, nvec, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
         // z forward (W_z(z), psi(z+1)) / backward (W_z(z-1), psi(z-1)), from registers
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256) k_step_zm(const char *__restrict__ W, con
                 o[k][q].im = fma(a, fma(R(-6), pc[k][q].im, acc[k][q].im), pc[k][q].im);
             }
         }
-        RecGroup<VP, VB, A16>::store(rout + (unsigned)i * rstride, o);
+        RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, nvec, t, T, o);
         // slide the column window
 #pragma unroll
         for (int k = 0; k < VB; ++k)
@@ -613,7 +613,7 @@ inline int il_spb(int nvec, int threads)
     return spb;
 }
 
-template <int VP, int WF, int VB, bool A16> cudaError_t step_il_launch(const StepArgs &a)
+template <int VP, int WF, int VB> cudaError_t step_il_launch(const StepArgs &a)
 {
     const int tx = a.nvec / VB;
     // a strip of spb consecutive x' per CTA; tile[0] > 0 sets spb explicitly
@@ -627,24 +627,24 @@ template <int VP, int WF, int VB, bool A16> cudaError_t step_il_launch(const Ste
     dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
     if (a.tile[1] > 0 && a.active == nullptr)  // W of the strip staged in shared memory
-        k_step_ilw<VP, WF, VB, A16><<<grid, block, 6 * ((spb * wfmt_bytes(WF) + 15) / 16 * 16), a.stream>>>(
+        k_step_ilw<VP, WF, VB><<<grid, block, 6 * ((spb * wfmt_bytes(WF) + 15) / 16 * 16), a.stream>>>(
             a.W, a.in, a.out, a.alpha, a.g, a.nvec);
     else if (occ)
-        k_step_il_occ<VP, WF, VB, A16><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g,
+        k_step_il_occ<VP, WF, VB><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g,
                                                                      a.nvec);
     else
-        k_step_il<VP, WF, VB, A16><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g, a.nvec);
+        k_step_il<VP, WF, VB><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g, a.nvec);
     return cudaGetLastError();
 }
 
-template <int VP, int WF, int VB, bool A16> cudaError_t step_zm_launch(const StepArgs &a)
+template <int VP, int WF, int VB> cudaError_t step_zm_launch(const StepArgs &a)
 {
     const int tx = a.nvec / VB;
     const int spb = il_spb(tx, a.threads);
     dim3 block(tx, spb);
     dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.nblk);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    k_step_zm<VP, WF, VB, A16><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g, a.nvec);
+    k_step_zm<VP, WF, VB><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g, a.nvec);
     return cudaGetLastError();
 }
 
@@ -657,20 +657,19 @@ template <int VP, int WF> cudaError_t step_zm_w(const StepArgs &a)
         int vb = a.vb > 0 ? a.vb : 1;
         if (a.nvec % vb != 0) vb = 1;
         if constexpr (VP == P_F32) {
-            const bool a16 = (a.nvec % 2 == 0);
             switch (vb) {
-            case 2: return a16 ? step_zm_launch<VP, WF, 2, true>(a) : step_zm_launch<VP, WF, 2, false>(a);
-            case 4: return a16 ? step_zm_launch<VP, WF, 4, true>(a) : step_zm_launch<VP, WF, 4, false>(a);
-            default: return step_zm_launch<VP, WF, 1, false>(a);
+            case 2: return step_zm_launch<VP, WF, 2>(a);
+            case 4: return step_zm_launch<VP, WF, 4>(a);
+            default: return step_zm_launch<VP, WF, 1>(a);
             }
         } else if constexpr (VP == P_F64) {
-            if (vb == 2) return step_zm_launch<VP, WF, 2, false>(a);
-            return step_zm_launch<VP, WF, 1, false>(a);
+            if (vb == 2) return step_zm_launch<VP, WF, 2>(a);
+            return step_zm_launch<VP, WF, 1>(a);
         } else {
             switch (vb) {
-            case 2: return step_zm_launch<VP, WF, 2, false>(a);
-            case 4: return step_zm_launch<VP, WF, 4, false>(a);
-            default: return step_zm_launch<VP, WF, 1, false>(a);
+            case 2: return step_zm_launch<VP, WF, 2>(a);
+            case 4: return step_zm_launch<VP, WF, 4>(a);
+            default: return step_zm_launch<VP, WF, 1>(a);
             }
         }
     }
@@ -687,20 +686,19 @@ template <int VP, int WF> cudaError_t step_il_w(const StepArgs &a)
         int vb = a.vb > 0 ? a.vb : 1;
         if (a.nvec % vb != 0) vb = 1;
         if constexpr (VP == P_F32) {
-            const bool a16 = (a.nvec % 2 == 0);
             switch (vb) {
-            case 2: return a16 ? step_il_launch<VP, WF, 2, true>(a) : step_il_launch<VP, WF, 2, false>(a);
-            case 4: return a16 ? step_il_launch<VP, WF, 4, true>(a) : step_il_launch<VP, WF, 4, false>(a);
-            default: return step_il_launch<VP, WF, 1, false>(a);
+            case 2: return step_il_launch<VP, WF, 2>(a);
+            case 4: return step_il_launch<VP, WF, 4>(a);
+            default: return step_il_launch<VP, WF, 1>(a);
             }
         } else if constexpr (VP == P_F64) {
-            if (vb == 2) return step_il_launch<VP, WF, 2, false>(a);
-            return step_il_launch<VP, WF, 1, false>(a);
+            if (vb == 2) return step_il_launch<VP, WF, 2>(a);
+            return step_il_launch<VP, WF, 1>(a);
         } else {
             switch (vb) {
-            case 2: return step_il_launch<VP, WF, 2, false>(a);
-            case 4: return step_il_launch<VP, WF, 4, false>(a);
-            default: return step_il_launch<VP, WF, 1, false>(a);
+            case 2: return step_il_launch<VP, WF, 2>(a);
+            case 4: return step_il_launch<VP, WF, 4>(a);
+            default: return step_il_launch<VP, WF, 1>(a);
             }
         }
     }

@@ -393,117 +393,128 @@ template <> struct VFmt<P_F16> : VFmtH<__half> {};
 template <> struct VFmt<P_BF16> : VFmtH<__nv_bfloat16> {};
 
 // --------------------------------------------------------------------------
-// Interleaved (vector-innermost) records: the nvec vectors of one site are
-// adjacent, record (block, i, v) at ((block * Ps + i) * nvec + v) * bytes.
-// A warp then covers consecutive (site, vector) pairs: vector loads are
-// contiguous and the W of a site is one broadcast for all its lanes.
-//   F64 : 3 x double2 (48 B)   F32 : 3 x float2 (24 B)   16-bit: 16 B record
+// Interleaved (vector-innermost) records.  The nvec vectors of one site form
+// one contiguous record group of nvec * bytes at (block * Ps + i) * nvec * bytes:
+//   F64 / F32: colour-major, [colour][vector] complex numbers (double2 /
+//              float2), so colour c of vectors w, w+1, ... is contiguous;
+//   16-bit   : one 16-byte record per vector {3 x half2, float scale}.
+// A warp covers consecutive (site, vector) pairs and the W of a site is one
+// broadcast for all its lanes.  A thread that owns VB vectors of a site takes
+// the load units t, t + T, t + 2T, ... (T = nvec / VB threads per site), a
+// unit being the vectors whose colour c fills one 16-byte word (two for F32,
+// one otherwise).  Consecutive threads then read consecutive 16-byte words:
+// every warp load and store covers whole 32-byte sectors.
 // --------------------------------------------------------------------------
 template <int P> struct VRec;
 
 template <> struct VRec<P_F64> {
     typedef double R;
-    static __device__ __forceinline__ void load(const char *rec, cpx<double> v[3])
+    static constexpr int U = 1;
+    // vector w of the group at grp (n vectors)
+    static __device__ __forceinline__ void load(const char *grp, int n, int w, cpx<double> v[3])
     {
-        const double2 *p = reinterpret_cast<const double2 *>(rec);
+        const double2 *p = reinterpret_cast<const double2 *>(grp) + w;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            double2 a = p[c];
+            double2 a = p[c * n];
             v[c].re = a.x;
             v[c].im = a.y;
         }
     }
-    static __device__ __forceinline__ void store(char *rec, const cpx<double> v[3])
+    static __device__ __forceinline__ void store(char *grp, int n, int w, const cpx<double> v[3])
     {
-        double2 *p = reinterpret_cast<double2 *>(rec);
+        double2 *p = reinterpret_cast<double2 *>(grp) + w;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p[c] = make_double2(v[c].re, v[c].im);
+        for (int c = 0; c < 3; ++c) p[c * n] = make_double2(v[c].re, v[c].im);
     }
 };
 
 template <> struct VRec<P_F32> {
     typedef float R;
-    static __device__ __forceinline__ void load(const char *rec, cpx<float> v[3])
+    static constexpr int U = 2;
+    static __device__ __forceinline__ void load(const char *grp, int n, int w, cpx<float> v[3])
     {
-        const float2 *p = reinterpret_cast<const float2 *>(rec);
+        const float2 *p = reinterpret_cast<const float2 *>(grp) + w;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float2 a = p[c];
+            float2 a = p[c * n];
             v[c].re = a.x;
             v[c].im = a.y;
         }
     }
-    static __device__ __forceinline__ void store(char *rec, const cpx<float> v[3])
+    static __device__ __forceinline__ void store(char *grp, int n, int w, const cpx<float> v[3])
     {
-        float2 *p = reinterpret_cast<float2 *>(rec);
+        float2 *p = reinterpret_cast<float2 *>(grp) + w;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p[c] = make_float2(v[c].re, v[c].im);
+        for (int c = 0; c < 3; ++c) p[c * n] = make_float2(v[c].re, v[c].im);
+    }
+    // the unit of vectors 2u, 2u+1 (n even): one 16-byte word per colour
+    static __device__ __forceinline__ void load2(const char *grp, int n, int u, cpx<float> a[3], cpx<float> b[3])
+    {
+        const float4 *p = reinterpret_cast<const float4 *>(grp) + u;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float4 q = p[c * (n >> 1)];
+            a[c].re = q.x;
+            a[c].im = q.y;
+            b[c].re = q.z;
+            b[c].im = q.w;
+        }
+    }
+    static __device__ __forceinline__ void store2(char *grp, int n, int u, const cpx<float> a[3], const cpx<float> b[3])
+    {
+        float4 *p = reinterpret_cast<float4 *>(grp) + u;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[c * (n >> 1)] = make_float4(a[c].re, a[c].im, b[c].re, b[c].im);
     }
 };
 
 template <typename H> struct VRecH {
     typedef float R;
-    static __device__ __forceinline__ void load(const char *rec, cpx<float> v[3])
+    static constexpr int U = 1;
+    static __device__ __forceinline__ void load(const char *grp, int, int w, cpx<float> v[3])
     {
-        VFmtH<H>::template load<false>(rec, 0, 0, v);
+        VFmtH<H>::template load<false>(grp, 0, w, v);
     }
-    static __device__ __forceinline__ void store(char *rec, const cpx<float> v[3])
+    static __device__ __forceinline__ void store(char *grp, int, int w, const cpx<float> v[3])
     {
-        VFmtH<H>::template store<false>(rec, 0, 0, v);
+        VFmtH<H>::template store<false>(grp, 0, w, v);
     }
 };
 template <> struct VRec<P_F16> : VRecH<__half> {};
 template <> struct VRec<P_BF16> : VRecH<__nv_bfloat16> {};
 
-// VB adjacent interleaved records (vectors v0 .. v0+VB-1 of one site).  With
-// A16 the group starts on a 16-byte boundary and is read with 16-byte loads
-// (FP32: 24*VB bytes = 1.5*VB words; needs VB even).
-template <int VP, int VB, bool A16> struct RecGroup {
-    typedef typename VRec<VP>::R R;
-    static __device__ __forceinline__ void load(const char *p, cpx<R> v[VB][3])
-    {
-#pragma unroll
-        for (int k = 0; k < VB; ++k) VRec<VP>::load(p + k * vfmt_bytes(VP), v[k]);
-    }
-    static __device__ __forceinline__ void store(char *p, const cpx<R> v[VB][3])
-    {
-#pragma unroll
-        for (int k = 0; k < VB; ++k) VRec<VP>::store(p + k * vfmt_bytes(VP), v[k]);
-    }
-};
+// Vector index of the k-th of the VB vectors that thread t (of T = nvec / VB
+// per site) owns.
+template <int VP, int VB> __device__ __forceinline__ int il_vec(int t, int T, int k)
+{
+    constexpr int U = VB % VRec<VP>::U == 0 ? VRec<VP>::U : 1;
+    return (t + (k / U) * T) * U + k % U;
+}
 
-template <int VB> struct RecGroup<P_F32, VB, true> {
-    static_assert(VB % 2 == 0, "16-byte FP32 record groups need an even count");
-    static __device__ __forceinline__ void load(const char *p, cpx<float> v[VB][3])
+// The VB vectors of thread t in the record group at grp (n vectors).
+template <int VP, int VB> struct RecGroup {
+    typedef typename VRec<VP>::R R;
+    static constexpr bool PAIRS = VRec<VP>::U == 2 && VB % 2 == 0;
+    static __device__ __forceinline__ void load(const char *grp, int n, int t, int T, cpx<R> v[VB][3])
     {
-        const float4 *q = reinterpret_cast<const float4 *>(p);
-        float f[6 * VB];
+        if constexpr (PAIRS) {
 #pragma unroll
-        for (int k = 0; k < 3 * VB / 2; ++k) {
-            float4 a = q[k];
-            f[4 * k] = a.x; f[4 * k + 1] = a.y; f[4 * k + 2] = a.z; f[4 * k + 3] = a.w;
+            for (int j = 0; j < VB / 2; ++j) VRec<VP>::load2(grp, n, t + j * T, v[2 * j], v[2 * j + 1]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < VB; ++k) VRec<VP>::load(grp, n, t + k * T, v[k]);
         }
-#pragma unroll
-        for (int k = 0; k < VB; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                v[k][c].re = f[6 * k + 2 * c];
-                v[k][c].im = f[6 * k + 2 * c + 1];
-            }
     }
-    static __device__ __forceinline__ void store(char *p, const cpx<float> v[VB][3])
+    static __device__ __forceinline__ void store(char *grp, int n, int t, int T, const cpx<R> v[VB][3])
     {
-        float f[6 * VB];
+        if constexpr (PAIRS) {
 #pragma unroll
-        for (int k = 0; k < VB; ++k)
+            for (int j = 0; j < VB / 2; ++j) VRec<VP>::store2(grp, n, t + j * T, v[2 * j], v[2 * j + 1]);
+        } else {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                f[6 * k + 2 * c] = v[k][c].re;
-                f[6 * k + 2 * c + 1] = v[k][c].im;
-            }
-        float4 *q = reinterpret_cast<float4 *>(p);
-#pragma unroll
-        for (int k = 0; k < 3 * VB / 2; ++k) q[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+            for (int k = 0; k < VB; ++k) VRec<VP>::store(grp, n, t + k * T, v[k]);
+        }
     }
 };
 

@@ -32,3 +32,11 @@ HEADLINE = dict(dims=(64, 64, 64, 96), links="near", eps=0.2, gauge_seed=1003, N
 SERVING = dict(configs=((16, 16, 16, 32), (32, 32, 32, 64), (48, 48, 48, 96)), gauge_seed=1004,
                vec_seed=2004, arrival_seed=3000, nvec=(1, 24), N=(10, 80), sigma_per_N=(0.05, 0.3),
                hbm_cap=120 * 2 ** 30)
+
+# Sink smearing in the many-source pattern of the baryon measurement (Sec. 6):
+# 72 sources/sinks smeared with one two-link field, n = 30.  Stand-in: 48^3 x 64
+# near-unit links (0.2), 72 dense Gaussian vectors on every slice (24 solved
+# propagators x 3 colour columns), sigma / N = 0.2, FP32 storage, one
+# multi-RHS batch.
+SINK_SMEAR = dict(dims=(48, 48, 48, 64), links="near", eps=0.2, gauge_seed=1005, vec_seed=2005,
+                  N=30, sigma=6.0, nvec=72, name="48^3x64 72 dense sink vectors N=30")

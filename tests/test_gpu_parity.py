@@ -474,3 +474,37 @@ def test_onelink_needs_links(ctx, T):
         ctx.smear_onelink(gid, x.to(torch.complex128), T.TLS_F64, 1, 3, 0.1, storage=T.TLS_F64)
     assert e.value.status == T.TLS_ERR_UNSUPPORTED
     ctx.free_gauge(gid)
+
+
+# ------------------------------------------------------------------ many-source sink smearing (Sec. 6)
+def test_sink_smear_pattern_small(ctx, T):
+    """72 dense vectors on every slice, n = 30, one W: the many-source batch against the oracle."""
+    dims = (8, 8, 8, 4)
+    w = workloads.SINK_SMEAR
+    U = gauge(dims, "near", 45, eps=0.2)
+    vecs = synth.gaussian_vectors(dims, w["nvec"], 46, dtype=torch.complex64)
+    want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), w["N"], w["sigma"])
+    got, norms = _run(ctx, T, U, dims, vecs, T.TLS_F32, T.TLS_F32, 18, T.TLS_KERNEL_MRHS, w["N"], w["sigma"], -1)
+    errs = per_vector_rel_l2(got, want)
+    assert max(errs) <= tol(T.TLS_F32, w["N"]), max(errs)
+    assert np.allclose(norms, (np.abs(got) ** 2).reshape(w["nvec"], -1).sum(1), rtol=1e-12, atol=0)
+
+
+def test_sink_smear_workload_sampled(ctx, T):
+    """48^3x64 with 72 dense vectors, n = 30 (the sink-smearing workload), sampled against the oracle."""
+    w = workloads.SINK_SMEAR
+    dims = w["dims"]
+    U = gauge_dev(dims, "near", w["gauge_seed"], eps=w["eps"], nd=4)
+    vecs = synth.gaussian_vectors(dims, w["nvec"], w["vec_seed"], dtype=torch.complex64, device="cuda")
+    samples = ((0, 0), (37, 29), (71, 63))
+    ref = {(v, t): vecs[v, t:t + 1].cpu().numpy().astype(np.complex128) for v, t in samples}
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.build_twolink(gid, T.TLS_F32, 18)
+    ctx.smear(gid, vecs, T.TLS_F32, w["nvec"], w["N"], w["sigma"], storage=T.TLS_F32, kernel=T.TLS_KERNEL_AUTO)
+    ctx.free_gauge(gid)
+    for (v, t), src in ref.items():
+        want = oracle.smear(oracle.twolink(U[t:t + 1].cpu().numpy()), src, w["N"], w["sigma"])
+        got = vecs[v, t:t + 1].cpu().numpy().astype(np.complex128)
+        assert rel_l2(got, want) <= tol(T.TLS_F32, w["N"])
+    del vecs, U
+    torch.cuda.empty_cache()
