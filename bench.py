@@ -76,6 +76,19 @@ def dist_setup(backend):
 PROFILED_TRAFFIC_PER_SITE = {}
 
 
+def kernel_symbol(kern_name: str, entry: dict) -> str:
+    """CUDA kernel that a tune-table entry launches (the name ncu lists)."""
+    if kern_name == "mrhs":
+        tile = tuple(entry.get("tile", (0, 0, 0)))
+        if tile[1] in (2, 3):
+            return "k_step_ilx"
+        if tile[1] == 1:
+            return "k_step_ilw"
+        return "k_step_il_occ" if entry.get("threads", 0) < 0 else "k_step_il"
+    return {"persistent": "k_persist", "mrhs_rows": "k_step_rows", "mrhs_zm": "k_step_zm",
+            "single": "k_step"}.get(kern_name, "?")
+
+
 def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
     """The largest value of x over all ranks (the job is as slow as its slowest rank)."""
     if ws <= 1:
@@ -347,6 +360,7 @@ def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0):
 
 def sink_run(T, ctx, device, stream, hbm_peak):
     """Sink smearing in the many-source pattern: 72 dense vectors, n = 30, one W."""
+    import torch
     from paper_2301_05518_gb300 import synth, workloads
     w = workloads.SINK_SMEAR
     dims, nvec, N, sigma = w["dims"], w["nvec"], w["N"], w["sigma"]
@@ -459,8 +473,7 @@ def our_arm(args):
     traffic = per_site * V if per_site else None  # bytes per launch (one step over all sites)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "traffic": traffic,
-            "kernel": {"persistent": "k_persist", "mrhs": "k_step_il", "mrhs_rows": "k_step_rows",
-                       "mrhs_zm": "k_step_zm", "single": "k_step"}.get(kern_name, "?"),
+            "kernel": kernel_symbol(kern_name, tune_best),
             "peak_source": peak_kind,
             "note": ("algorithmic bytes = W once + psi read once + psi written once per site and "
                      "step; persistent launches count all N steps (effective GB/s)")}

@@ -250,8 +250,11 @@ typedef struct {
                             /* per CTA (a strip along x'); persistent kernel:  */
                             /* tile[0] > 0 sets the L2 budget of one group of  */
                             /* blocks in MB (default 48); multi-RHS kernel:    */
-                            /* tile[1] > 0 stages the strip's W in shared      */
-                            /* memory; tile[2] unused                          */
+                            /* tile[1] = 1 stages the strip's W in shared      */
+                            /* memory, tile[1] = 2 as well and applies it with */
+                            /* packed FP32 pair FMAs (not FP64), tile[1] = 3   */
+                            /* like 2 with all vector loads issued up front;   */
+                            /* tile[2] unused                                  */
     double ms_per_step;     /* measured time of one smearing step              */
 } tls_tune_entry;
 

@@ -355,6 +355,157 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
 }
 
 // --------------------------------------------------------------------------
+// Interleaved multi-RHS step with packed FP32 pairs (fma.rn.f32x2).
+// The strip's six W sets are staged in shared memory as one 16-byte word per
+// complex element, already broadcast for a paired complex multiply-add:
+//   forward  W(x)       element (r, k):            {re, re, -im, im}
+//   backward W(x - 2d)  element (k, r) (the dagger): {re, re, im, -im}
+// so that acc_r += w * p is two packed FMAs on (re, im) pairs,
+//   acc = fma2({re, re}, {p.re, p.im}, acc);  acc = fma2({-im, im}, {p.im, p.re}, acc)
+// which performs, lane by lane, the same FMA sequence as cmac / cmacc: the
+// results are bitwise equal to every other kernel.  Arithmetic in FP32 (FP32
+// and 16-bit storage).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2swap(float2 a) { return make_float2(a.y, a.x); }
+
+template <int VP, int WF, int VB, bool PRE>
+__global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, const char *__restrict__ in,
+                                                  char *__restrict__ out, const double *__restrict__ alpha,
+                                                  SubGeom g, int nvec)
+{
+    static_assert(VP != P_F64, "packed FP32 pairs only");
+    constexpr int WB = wfmt_bytes(WF);
+    constexpr int VBY = vfmt_bytes(VP);
+    extern __shared__ __align__(16) float4 wpk[];  // [set 6][element 9][site spb]
+    const int spb = blockDim.y;
+    const int x0 = blockIdx.x * spb;
+    const int yq = blockIdx.y;
+    const int blk = blockIdx.z / g.hz;
+    const int zq = blockIdx.z - blk * g.hz;
+    const int sy = g.hx, sz = g.hx * g.hy;
+    const int row = zq * sz + yq * sy;
+    const char *wb = W + (int64_t)blk * 3 * g.Ps * WB;
+    const int nsite = min(spb, g.hx - x0);
+    const int k = threadIdx.y;
+    const bool act = k < nsite;
+    const int t = threadIdx.x, T = nvec / VB;
+    const int xq = x0 + k;
+    const int i = row + xq;
+    int nb[7];  // the six hops in the order of site_step, then the site itself
+    nb[0] = xq == g.hx - 1 ? i - (g.hx - 1) : i + 1;
+    nb[1] = xq == 0 ? i + (g.hx - 1) : i - 1;
+    nb[2] = yq == g.hy - 1 ? i - (g.hy - 1) * sy : i + sy;
+    nb[3] = yq == 0 ? i + (g.hy - 1) * sy : i - sy;
+    nb[4] = zq == g.hz - 1 ? i - (g.hz - 1) * sz : i + sz;
+    nb[5] = zq == 0 ? i + (g.hz - 1) * sz : i - sz;
+    nb[6] = i;
+    const char *rin = in + (int64_t)blk * g.Ps * nvec * VBY;
+    char *rout = out + (int64_t)blk * g.Ps * nvec * VBY;
+    const unsigned rstride = (unsigned)nvec * VBY;
+    // PRE: all seven record groups are requested before the W staging, so
+    // their latencies overlap one another and the staging.
+    cpx<float> pre[PRE ? 7 : 1][VB][3];
+    if constexpr (PRE) {
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) RecGroup<VP, VB>::load(rin + (unsigned)nb[q] * rstride, nvec, t, T, pre[q]);
+        }
+    }
+    {
+        // stage: (set q, site kk) per thread; q = 2d + (0 forward, 1 backward)
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        for (int e = tid; e < 6 * nsite; e += blockDim.x * blockDim.y) {
+            const int q = e / nsite, kk = e - q * nsite;
+            const int d = q >> 1, xs = x0 + kk;
+            int gi;
+            if (q == 1)
+                gi = row + (xs == 0 ? g.hx - 1 : xs - 1);
+            else if (q == 3)
+                gi = zq * sz + (yq == 0 ? g.hy - 1 : yq - 1) * sy + xs;
+            else if (q == 5)
+                gi = (zq == 0 ? g.hz - 1 : zq - 1) * sz + yq * sy + xs;
+            else
+                gi = row + xs;
+            cpx<float> m[9];
+            WFmt<WF>::load(wb + (int64_t)d * g.Ps * WB, g.Ps, gi, m);
+            float4 *dst = wpk + q * 9 * spb + kk;
+            if (q & 1) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const cpx<float> w = m[c * 3 + r];
+                        dst[(r * 3 + c) * spb] = make_float4(w.re, w.re, w.im, -w.im);
+                    }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 9; ++j) dst[j * spb] = make_float4(m[j].re, m[j].re, -m[j].im, m[j].im);
+            }
+        }
+    }
+    __syncthreads();
+    if (!act) return;
+    float2 acc[VB][3];
+#pragma unroll
+    for (int v = 0; v < VB; ++v)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) acc[v][r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        cpx<float> pl[VB][3];
+        if constexpr (!PRE) RecGroup<VP, VB>::load(rin + (unsigned)nb[q] * rstride, nvec, t, T, pl);
+        const float4 *wq = wpk + q * 9 * spb + k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float2 p[VB], ps[VB];
+#pragma unroll
+            for (int v = 0; v < VB; ++v) {
+                cpx<float> x;
+                if constexpr (PRE)
+                    x = pre[q][v][c];
+                else
+                    x = pl[v][c];
+                p[v] = make_float2(x.re, x.im);
+                ps[v] = f2swap(p[v]);
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float4 w = wq[(r * 3 + c) * spb];
+                const float2 wa = make_float2(w.x, w.y), wc = make_float2(w.z, w.w);
+#pragma unroll
+                for (int v = 0; v < VB; ++v) {
+                    acc[v][r] = __ffma2_rn(wa, p[v], acc[v][r]);
+                    acc[v][r] = __ffma2_rn(wc, ps[v], acc[v][r]);
+                }
+            }
+        }
+    }
+    cpx<float> cc[VB][3], o[VB][3];
+    if constexpr (PRE) {
+#pragma unroll
+        for (int v = 0; v < VB; ++v)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) cc[v][r] = pre[6 % (PRE ? 7 : 1)][v][r];
+    } else {
+        RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, nvec, t, T, cc);
+    }
+    const float2 m6 = make_float2(-6.f, -6.f);
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+        const float a = (float)alpha[il_vec<VP, VB>(t, T, v)];
+        const float2 a2 = make_float2(a, a);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float2 c2 = make_float2(cc[v][r].re, cc[v][r].im);
+            const float2 u = __ffma2_rn(a2, __ffma2_rn(m6, c2, acc[v][r]), c2);
+            o[v][r].re = u.x;
+            o[v][r].im = u.y;
+        }
+    }
+    RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, nvec, t, T, o);
+}
+
+// --------------------------------------------------------------------------
 // Multi-RHS step on the interleaved layout, marching along z'.
 // CTA = (nvec/VB, spb): threadIdx.x picks VB adjacent vectors, threadIdx.y
 // one of spb consecutive x' of row y' = blockIdx.y in block blockIdx.z; each
@@ -622,11 +773,24 @@ template <int VP, int WF, int VB> cudaError_t step_il_launch(const StepArgs &a)
     const int cap = occ ? 128 : 256;
     int spb = a.tile[0] > 0 ? a.tile[0] : il_spb(tx, occ ? 128 : a.threads);
     spb = std::max(1, std::min(spb, cap / tx));
+    const bool packed = (a.tile[1] == 2 || a.tile[1] == 3) && a.active == nullptr && VP != P_F64;
+    constexpr int kPackB = 6 * 9 * 16;  // W packs per site of the packed kernel
+    if (packed) spb = std::min(spb, (48 << 10) / kPackB);  // within the default dynamic shared memory
     if (tx * spb > cap) return cudaErrorInvalidConfiguration;
     dim3 block(tx, spb);
     dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-    if (a.tile[1] > 0 && a.active == nullptr)  // W of the strip staged in shared memory
+    if (packed) {
+        // packed FP32 pairs with W packs in shared memory; 3 = all records requested up front
+        if constexpr (VP != P_F64) {
+            if (a.tile[1] == 3)
+                k_step_ilx<VP, WF, VB, true><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g,
+                                                                                      a.nvec);
+            else
+                k_step_ilx<VP, WF, VB, false><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha,
+                                                                                       a.g, a.nvec);
+        }
+    } else if (a.tile[1] > 0 && a.active == nullptr)  // W of the strip staged in shared memory
         k_step_ilw<VP, WF, VB><<<grid, block, 6 * ((spb * wfmt_bytes(WF) + 15) / 16 * 16), a.stream>>>(
             a.W, a.in, a.out, a.alpha, a.g, a.nvec);
     else if (occ)

@@ -36,6 +36,12 @@ std::vector<Cand> candidates(int nvec, int storage, bool rows)
         if (tx <= 128) c.push_back({TLS_KERNEL_MRHS, vb, -128, {0, 0, 0}});
         for (int t : {128, 256})  // W of the strip staged in shared memory
             if (t >= tx) c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 1, 0}});
+        if (storage != TLS_F64)  // packed FP32 pairs with broadcast W in shared memory
+            for (int t : {128, 256})
+                if (t >= tx) {
+                    c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 2, 0}});
+                    c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 3, 0}});  // records requested up front
+                }
         if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0, {0, 0, 0}});
     }
     const int vmax = storage == TLS_F64 ? 4 : 8;

@@ -420,23 +420,36 @@ def test_rows_kernel_at_headline_shape_sampled(ctx, T):
         assert rel_l2(vecs[v, 1:2].cpu().numpy().astype(np.complex128), want) <= 2e-6 * 8
 
 
-@pytest.mark.parametrize("tile,vb", [((2, 0, 0), 2), ((5, 0, 0), 1), ((8, 0, 0), 4), ((3, 0, 0), 2),
-                                     ((0, 1, 0), 2), ((5, 1, 0), 4), ((3, 1, 0), 1)])
-def test_interleaved_strips_bitwise_equal_single(ctx, T, tile, vb):
-    """Explicit strip lengths of the multi-RHS kernel, including ones that do not divide hx."""
+@pytest.mark.parametrize("tile,vb,storage", [((2, 0, 0), 2, "F32"), ((5, 0, 0), 1, "F32"), ((8, 0, 0), 4, "F32"),
+                                             ((3, 0, 0), 2, "F32"), ((0, 1, 0), 2, "F32"), ((5, 1, 0), 4, "F32"),
+                                             ((3, 1, 0), 1, "F32"), ((0, 2, 0), 2, "F32"), ((5, 2, 0), 4, "F32"),
+                                             ((3, 2, 0), 1, "F32"), ((0, 2, 0), 2, "F16"), ((4, 2, 0), 4, "BF16"),
+                                             ((7, 2, 0), 1, "F16"), ((0, 3, 0), 2, "F32"), ((5, 3, 0), 4, "F16"),
+                                             ((3, 3, 0), 1, "F32"), ((0, 3, 0), 4, "BF16")])
+@pytest.mark.parametrize("recon", [18, 12])
+def test_interleaved_strips_bitwise_equal_single(ctx, T, tile, vb, storage, recon):
+    """Strip lengths (some not dividing hx), W staged in shared memory (tile[1] = 1) and the
+    packed FP32 pair kernel (tile[1] = 2) == one vector per launch, bitwise."""
     dims = (12, 10, 8, 2)
     nvec = 8
+    st = getattr(T, "TLS_" + storage)
     U = gauge(dims, "haar", 35)
     vecs = synth.gaussian_vectors(dims, nvec, 36, dtype=torch.complex64)
     gid = ctx.load_gauge(U, 4, dims)
-    ctx.build_twolink(gid, T.TLS_F32, 18)
-    ctx.tune_set(gid, nvec, T.TLS_F32, T.TLS_ALL_T, T.TLS_KERNEL_MRHS, vb, 0, tile)
+    ctx.build_twolink(gid, T.TLS_F32, recon)
+    ctx.tune_set(gid, nvec, st, T.TLS_ALL_T, T.TLS_KERNEL_MRHS, vb, 0, tile)
     a = vecs.clone().cuda()
-    ctx.smear(gid, a, T.TLS_F32, nvec, 6, 1.3, storage=T.TLS_F32, kernel=T.TLS_KERNEL_AUTO)
+    ctx.set_profiling(True)
+    ctx.smear(gid, a, T.TLS_F32, nvec, 6, 1.3, storage=st, kernel=T.TLS_KERNEL_AUTO)
+    assert ctx.get_profile()["kernel"] == T.TLS_KERNEL_MRHS
+    ctx.set_profiling(False)
     b = vecs.clone().cuda()
-    ctx.smear(gid, b, T.TLS_F32, nvec, 6, 1.3, storage=T.TLS_F32, kernel=T.TLS_KERNEL_SINGLE)
+    ctx.smear(gid, b, T.TLS_F32, nvec, 6, 1.3, storage=st, kernel=T.TLS_KERNEL_SINGLE)
     ctx.free_gauge(gid)
     assert torch.equal(a, b)
+    if storage == "F32" and recon == 18:
+        want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), 6, 1.3)
+        assert max(per_vector_rel_l2(a.cpu().numpy().astype(np.complex128), want)) <= 2e-6 * 6
 
 
 # ------------------------------------------------------------------ one-link Gaussian smearing (Eq. 2-3)
