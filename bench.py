@@ -73,7 +73,12 @@ def dist_setup(backend):
 # profiles/ (64^3x4 lattice, 24 vectors, FP32, W FP32-18; the full 64^3x96 launch
 # scales by the number of sites).  Keyed by (kernel, vectors per thread,
 # tile); a configuration without a capture of its current code reports null.
-PROFILED_TRAFFIC_PER_SITE = {}
+PROFILED_TRAFFIC_PER_SITE = {
+    ("mrhs", 2, (0, 2, 0)): 1338.2,  # k_step_ilx, profiles/k_step_ilx_64x64x64x4_24vec_f32.md
+    ("mrhs", 4, (0, 2, 0)): 1338.2,
+    ("mrhs", 2, (0, 0, 0)): 1338.0,  # k_step_il, profiles/k_step_il_64x64x64x4_24vec_f32.md
+    ("mrhs", 4, (0, 0, 0)): 1339.7,
+}
 
 
 def kernel_symbol(kern_name: str, entry: dict) -> str:
@@ -82,7 +87,7 @@ def kernel_symbol(kern_name: str, entry: dict) -> str:
         tile = tuple(entry.get("tile", (0, 0, 0)))
         if tile[1] in (2, 3):
             return "k_step_ilx"
-        if tile[1] == 1:
+        if tile[1] in (1, 4):
             return "k_step_ilw"
         return "k_step_il_occ" if entry.get("threads", 0) < 0 else "k_step_il"
     return {"persistent": "k_persist", "mrhs_rows": "k_step_rows", "mrhs_zm": "k_step_zm",

@@ -253,8 +253,9 @@ typedef struct {
                             /* tile[1] = 1 stages the strip's W in shared      */
                             /* memory, tile[1] = 2 as well and applies it with */
                             /* packed FP32 pair FMAs (not FP64), tile[1] = 3   */
-                            /* like 2 with all vector loads issued up front;   */
-                            /* tile[2] unused                                  */
+                            /* like 2 with all vector loads issued up front,   */
+                            /* tile[1] = 4 stages W as stored and applies it   */
+                            /* with packed FP32 pair FMAs; tile[2] unused      */
     double ms_per_step;     /* measured time of one smearing step              */
 } tls_tune_entry;
 

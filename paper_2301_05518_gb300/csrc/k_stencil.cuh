@@ -244,6 +244,61 @@ __global__ void __launch_bounds__(128, 8) k_step_il_occ(const char *__restrict__
     step_il_body<VP, WF, VB>(W, in, out, alpha, active, g, nvec);
 }
 
+// Packed FP32 pair forms of mv_add / mdv_add for VB vectors: every (re, im)
+// accumulator gets, lane by lane, the FMA sequence of cmac / cmacc, with the
+// broadcast W pairs built once per element for all VB vectors.
+__device__ __forceinline__ float2 f2swap(float2 a) { return make_float2(a.y, a.x); }
+
+template <int VB>
+__device__ __forceinline__ void mv_add_x2(const cpx<float> m[9], const cpx<float> p[VB][3], float2 acc[VB][3])
+{
+    float2 pp[VB][3], ps[VB][3];
+#pragma unroll
+    for (int v = 0; v < VB; ++v)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pp[v][c] = make_float2(p[v][c].re, p[v][c].im);
+            ps[v][c] = f2swap(pp[v][c]);
+        }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const cpx<float> w = m[r * 3 + c];
+            const float2 wa = make_float2(w.re, w.re), wc = make_float2(-w.im, w.im);
+#pragma unroll
+            for (int v = 0; v < VB; ++v) {
+                acc[v][r] = __ffma2_rn(wa, pp[v][c], acc[v][r]);
+                acc[v][r] = __ffma2_rn(wc, ps[v][c], acc[v][r]);
+            }
+        }
+}
+
+template <int VB>
+__device__ __forceinline__ void mdv_add_x2(const cpx<float> m[9], const cpx<float> p[VB][3], float2 acc[VB][3])
+{
+    float2 pp[VB][3], ps[VB][3];
+#pragma unroll
+    for (int v = 0; v < VB; ++v)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pp[v][c] = make_float2(p[v][c].re, p[v][c].im);
+            ps[v][c] = f2swap(pp[v][c]);
+        }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const cpx<float> w = m[c * 3 + r];
+            const float2 wa = make_float2(w.re, w.re), wc = make_float2(w.im, -w.im);
+#pragma unroll
+            for (int v = 0; v < VB; ++v) {
+                acc[v][r] = __ffma2_rn(wa, pp[v][c], acc[v][r]);
+                acc[v][r] = __ffma2_rn(wc, ps[v][c], acc[v][r]);
+            }
+        }
+}
+
 // --------------------------------------------------------------------------
 // Interleaved multi-RHS step with the strip's W staged in shared memory.
 // The CTA's spb sites need six W matrices each (W_d(x) and W_d(x - 2d) for
@@ -252,7 +307,7 @@ __global__ void __launch_bounds__(128, 8) k_step_il_occ(const char *__restrict__
 // from there: one cooperative copy instead of 30 global loads per thread.
 // Same FMA sequence as site_step.
 // --------------------------------------------------------------------------
-template <int VP, int WF, int VB>
+template <int VP, int WF, int VB, bool PK>
 __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, const char *__restrict__ in,
                                                   char *__restrict__ out, const double *__restrict__ alpha,
                                                   SubGeom g, int nvec)
@@ -285,13 +340,15 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
     };
     const int setB = (spb * WB + 15) / 16 * 16;  // one set: planes of spb words, 16-byte aligned
     {
-        const int words = NQ + (REM ? 1 : 0);
+        constexpr int words = NQ + (REM ? 1 : 0);
         const int total = 6 * nsite * words;
         const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        // site index fastest: consecutive lanes copy consecutive words of one plane
         for (int e = tid; e < total; e += blockDim.x * blockDim.y) {
-            const int j = e % words;
-            const int k = (e / words) % nsite;
-            const int q = e / (words * nsite);
+            const int r = e / nsite;
+            const int k = e - r * nsite;
+            const int q = r / words;
+            const int j = r - q * words;
             const int d = q >> 1;
             const char *src = wb + (int64_t)d * g.Ps * WB;
             char *dst = reinterpret_cast<char *>(wsm) + q * setB;
@@ -323,32 +380,65 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
     char *rout = out + (int64_t)blk * g.Ps * nvec * VBY;
     const unsigned rstride = (unsigned)nvec * VBY;
     const char *ws = reinterpret_cast<const char *>(wsm);
-    cpx<R> acc[VB][3];
-#pragma unroll
-    for (int kk = 0; kk < VB; ++kk)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[kk][c].re = acc[kk][c].im = R(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        cpx<R> m[9], p[VB][3];
-        WFmt<WF>::load(ws + (2 * d) * setB, spb, k, m);
-        RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, nvec, t, T, p);
-#pragma unroll
-        for (int kk = 0; kk < VB; ++kk) mv_add(m, p[kk], acc[kk]);
-        WFmt<WF>::load(ws + (2 * d + 1) * setB, spb, k, m);
-        RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, nvec, t, T, p);
-#pragma unroll
-        for (int kk = 0; kk < VB; ++kk) mdv_add(m, p[kk], acc[kk]);
-    }
     cpx<R> c[VB][3], o[VB][3];
-    RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, nvec, t, T, c);
+    if constexpr (PK) {
+        // packed FP32 pairs: the same FMA sequence lane by lane (VP is not FP64)
+        float2 acc[VB][3];
 #pragma unroll
-    for (int kk = 0; kk < VB; ++kk) {
-        const R a = (R)alpha[il_vec<VP, VB>(t, T, kk)];
+        for (int kk = 0; kk < VB; ++kk)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            o[kk][q].re = fma(a, fma(R(-6), c[kk][q].re, acc[kk][q].re), c[kk][q].re);
-            o[kk][q].im = fma(a, fma(R(-6), c[kk][q].im, acc[kk][q].im), c[kk][q].im);
+            for (int q = 0; q < 3; ++q) acc[kk][q] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            cpx<float> m[9], p[VB][3];
+            WFmt<WF>::load(ws + (2 * d) * setB, spb, k, m);
+            RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, nvec, t, T, p);
+            mv_add_x2<VB>(m, p, acc);
+            WFmt<WF>::load(ws + (2 * d + 1) * setB, spb, k, m);
+            RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, nvec, t, T, p);
+            mdv_add_x2<VB>(m, p, acc);
+        }
+        RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, nvec, t, T, c);
+        const float2 m6 = make_float2(-6.f, -6.f);
+#pragma unroll
+        for (int kk = 0; kk < VB; ++kk) {
+            const float a = (float)alpha[il_vec<VP, VB>(t, T, kk)];
+            const float2 a2 = make_float2(a, a);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float2 c2 = make_float2(c[kk][q].re, c[kk][q].im);
+                const float2 u = __ffma2_rn(a2, __ffma2_rn(m6, c2, acc[kk][q]), c2);
+                o[kk][q].re = u.x;
+                o[kk][q].im = u.y;
+            }
+        }
+    } else {
+        cpx<R> acc[VB][3];
+#pragma unroll
+        for (int kk = 0; kk < VB; ++kk)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) acc[kk][q].re = acc[kk][q].im = R(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            cpx<R> m[9], p[VB][3];
+            WFmt<WF>::load(ws + (2 * d) * setB, spb, k, m);
+            RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, nvec, t, T, p);
+#pragma unroll
+            for (int kk = 0; kk < VB; ++kk) mv_add(m, p[kk], acc[kk]);
+            WFmt<WF>::load(ws + (2 * d + 1) * setB, spb, k, m);
+            RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, nvec, t, T, p);
+#pragma unroll
+            for (int kk = 0; kk < VB; ++kk) mdv_add(m, p[kk], acc[kk]);
+        }
+        RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, nvec, t, T, c);
+#pragma unroll
+        for (int kk = 0; kk < VB; ++kk) {
+            const R a = (R)alpha[il_vec<VP, VB>(t, T, kk)];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                o[kk][q].re = fma(a, fma(R(-6), c[kk][q].re, acc[kk][q].re), c[kk][q].re);
+                o[kk][q].im = fma(a, fma(R(-6), c[kk][q].im, acc[kk][q].im), c[kk][q].im);
+            }
         }
     }
     RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, nvec, t, T, o);
@@ -366,8 +456,6 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
 // results are bitwise equal to every other kernel.  Arithmetic in FP32 (FP32
 // and 16-bit storage).
 // --------------------------------------------------------------------------
-__device__ __forceinline__ float2 f2swap(float2 a) { return make_float2(a.y, a.x); }
-
 template <int VP, int WF, int VB, bool PRE>
 __global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, const char *__restrict__ in,
                                                   char *__restrict__ out, const double *__restrict__ alpha,
@@ -773,9 +861,15 @@ template <int VP, int WF, int VB> cudaError_t step_il_launch(const StepArgs &a)
     const int cap = occ ? 128 : 256;
     int spb = a.tile[0] > 0 ? a.tile[0] : il_spb(tx, occ ? 128 : a.threads);
     spb = std::max(1, std::min(spb, cap / tx));
+    spb = std::min(spb, a.g.hx);  // a strip never spans more than one row
     const bool packed = (a.tile[1] == 2 || a.tile[1] == 3) && a.active == nullptr && VP != P_F64;
+    const bool staged = a.tile[1] > 0 && a.active == nullptr;
     constexpr int kPackB = 6 * 9 * 16;  // W packs per site of the packed kernel
-    if (packed) spb = std::min(spb, (48 << 10) / kPackB);  // within the default dynamic shared memory
+    // shared memory within the default dynamic limit (48 KB)
+    if (packed)
+        spb = std::min(spb, (48 << 10) / kPackB);
+    else if (staged)
+        spb = std::min(spb, ((48 << 10) / 6 - 16) / wfmt_bytes(WF));
     if (tx * spb > cap) return cudaErrorInvalidConfiguration;
     dim3 block(tx, spb);
     dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
@@ -790,8 +884,13 @@ template <int VP, int WF, int VB> cudaError_t step_il_launch(const StepArgs &a)
                 k_step_ilx<VP, WF, VB, false><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha,
                                                                                        a.g, a.nvec);
         }
+    } else if (a.tile[1] == 4 && a.active == nullptr && VP != P_F64) {
+        // W of the strip staged in shared memory as stored, packed FP32 pair FMAs
+        if constexpr (VP != P_F64)
+            k_step_ilw<VP, WF, VB, true><<<grid, block, 6 * ((spb * wfmt_bytes(WF) + 15) / 16 * 16), a.stream>>>(
+                a.W, a.in, a.out, a.alpha, a.g, a.nvec);
     } else if (a.tile[1] > 0 && a.active == nullptr)  // W of the strip staged in shared memory
-        k_step_ilw<VP, WF, VB><<<grid, block, 6 * ((spb * wfmt_bytes(WF) + 15) / 16 * 16), a.stream>>>(
+        k_step_ilw<VP, WF, VB, false><<<grid, block, 6 * ((spb * wfmt_bytes(WF) + 15) / 16 * 16), a.stream>>>(
             a.W, a.in, a.out, a.alpha, a.g, a.nvec);
     else if (occ)
         k_step_il_occ<VP, WF, VB><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g,
