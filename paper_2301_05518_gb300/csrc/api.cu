@@ -649,7 +649,9 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     size_t a_bytes = (size_t)vs * G;
     s = ensure(ctx, ctx->A, a_bytes, "tls_smear: vector buffer A");
     if (s == TLS_OK) s = ensure(ctx, ctx->B, a_bytes, "tls_smear: vector buffer B");
-    if (s == TLS_OK) s = ensure(ctx, ctx->alpha, sizeof(double) * nvec, "tls_smear: alpha");
+    // alpha per vector in FP64, then the same rounded to FP32 (read by the FP32-arithmetic kernels)
+    const size_t alpha_bytes = sizeof(double) * nvec + sizeof(float) * nvec;
+    if (s == TLS_OK) s = ensure(ctx, ctx->alpha, alpha_bytes, "tls_smear: alpha");
     if (s == TLS_OK && norms_out)
         s = ensure(ctx, ctx->partials, sizeof(double) * kNormParts * nvec, "tls_smear: partials");
     if (s == TLS_OK && norms_out) s = ensure(ctx, ctx->norms, sizeof(double) * nvec, "tls_smear: norms");
@@ -659,7 +661,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     if (ctx->h_alpha_n < (size_t)nvec) {
         if (ctx->h_alpha) cudaFreeHost(ctx->h_alpha);
         ctx->h_alpha = nullptr;
-        cudaError_t e = cudaMallocHost(&ctx->h_alpha, sizeof(double) * nvec);
+        cudaError_t e = cudaMallocHost(&ctx->h_alpha, alpha_bytes);
         if (e != cudaSuccess) return cuda_fail(e, "tls_smear: pinned alpha");
         ctx->h_alpha_n = nvec;
     }
@@ -698,6 +700,8 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
 
     const double a = N > 0 ? (op == 0 ? width / (4.0 * N) : width) : 0.0;
     for (int v = 0; v < nvec; ++v) ctx->h_alpha[v] = a;
+    float *h_alphaf = reinterpret_cast<float *>(ctx->h_alpha + nvec);
+    for (int v = 0; v < nvec; ++v) h_alphaf[v] = (float)a;  // round to nearest, as the kernels' conversion
 
     cudaError_t e = cudaSuccess;
     int64_t launches = 0, iter_launches = 0;
@@ -718,7 +722,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     mark(0);
     e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->alpha.p, ctx->h_alpha, sizeof(double) * nvec, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(ctx->alpha.p, ctx->h_alpha, alpha_bytes, cudaMemcpyHostToDevice, st);
 
     // Caller buffer (device) or staging copy of the selected slices.
     const char *src_io = nullptr;
@@ -758,6 +762,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         mark(3);
         char *result = (char *)ctx->A.p;
         const double *alpha_g = (const double *)ctx->alpha.p + g0;
+        const float *alphaf_g = reinterpret_cast<const float *>((const double *)ctx->alpha.p + nvec) + g0;
         if (N > 0 && e == cudaSuccess) {
             if (kern == TLS_KERNEL_PERSISTENT) {
                 pa.W = W0;
@@ -805,6 +810,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
                         sa.in = (it & 1) ? y : x;
                         sa.out = (it & 1) ? x : y;
                         sa.alpha = alpha_g + gi;
+                        sa.alphaf = alphaf_g + gi;
                         e = op == 1                     ? launch_hop(sa)
                             : kern == TLS_KERNEL_MRHS_ROWS ? launch_step_rows(sa, ctx->d_err)
                             : kern == TLS_KERNEL_MRHS_ZM ? launch_step_zm(sa)

@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(512) k_hop_il(const char *__restrict__ L1, con
     bw[1] = yq == 0 ? i + (g.hy - 1) * sy : i - sy;
     fw[2] = zq == g.hz - 1 ? i - (g.hz - 1) * sz : i + sz;
     bw[2] = zq == 0 ? i + (g.hz - 1) * sz : i - sz;
-    const unsigned rstride = (unsigned)nvec * VBY;
+    const unsigned rstride = (unsigned)nvec * VRec<VP>::SB;  // site stride
+    const int cs = g.Ps * nvec;                                    // colour planes
     auto recs = [&](int b) { return in + (int64_t)b * g.Ps * nvec * VBY; };
     auto links = [&](int b, int d) { return L1 + ((int64_t)b * 3 + d) * g.Ps * WB; };
     cpx<R> acc[VB][3];
@@ -55,16 +56,16 @@ __global__ void __launch_bounds__(512) k_hop_il(const char *__restrict__ L1, con
         const int i_b = odd ? i : bw[d];
         cpx<R> m[9], p[VB][3];
         WFmt<WF>::load(links(blk, d), g.Ps, i, m);
-        RecGroup<VP, VB>::load(recs(nb) + (unsigned)i_f * rstride, nvec, t, T, p);
+        RecGroup<VP, VB>::load(recs(nb) + (unsigned)i_f * rstride, cs, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
         WFmt<WF>::load(links(nb, d), g.Ps, i_b, m);
-        RecGroup<VP, VB>::load(recs(nb) + (unsigned)i_b * rstride, nvec, t, T, p);
+        RecGroup<VP, VB>::load(recs(nb) + (unsigned)i_b * rstride, cs, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
     }
     cpx<R> c[VB][3], o[VB][3];
-    RecGroup<VP, VB>::load(recs(blk) + (unsigned)i * rstride, nvec, t, T, c);
+    RecGroup<VP, VB>::load(recs(blk) + (unsigned)i * rstride, cs, t, T, c);
 #pragma unroll
     for (int k = 0; k < VB; ++k) {
         const R a = (R)alpha[il_vec<VP, VB>(t, T, k)];
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(512) k_hop_il(const char *__restrict__ L1, con
             o[k][q].im = fma(a, acc[k][q].im, c[k][q].im);
         }
     }
-    RecGroup<VP, VB>::store(out + ((int64_t)blk * g.Ps + i) * nvec * VBY, nvec, t, T, o);
+    RecGroup<VP, VB>::store(out + (int64_t)blk * g.Ps * nvec * VBY + (unsigned)i * rstride, cs, t, T, o);
 }
 
 template <int VP, int WF, int VB> cudaError_t hop_launch(const StepArgs &a)

@@ -264,7 +264,8 @@ __global__ void k_pack_il(const IO *__restrict__ src, int64_t svs, char *__restr
         val[k].re = (R)p[2 * k];
         val[k].im = (R)p[2 * k + 1];
     }
-    VRec<VP>::store(dst + ((int64_t)b * g.Ps + i) * rec_n * vfmt_bytes(VP), rec_n, rec_v0 + v, val);
+    VRec<VP>::store(dst + (int64_t)b * g.Ps * rec_n * vfmt_bytes(VP) + (int64_t)i * rec_n * VRec<VP>::SB, g.Ps * rec_n,
+                    rec_v0 + v, val);
 }
 
 template <typename IO, int VP>
@@ -281,7 +282,8 @@ __global__ void k_unpack_il(const char *__restrict__ src, IO *__restrict__ dst, 
     const int64_t site = (((int64_t)t * Lz + c.z) * Ly + c.y) * Lx + c.x;
     typedef typename VRec<VP>::R R;
     cpx<R> val[3];
-    VRec<VP>::load(src + ((int64_t)b * g.Ps + i) * rec_n * vfmt_bytes(VP), rec_n, rec_v0 + v, val);
+    VRec<VP>::load(src + (int64_t)b * g.Ps * rec_n * vfmt_bytes(VP) + (int64_t)i * rec_n * VRec<VP>::SB, g.Ps * rec_n,
+                   rec_v0 + v, val);
     IO *p = dst + ((int64_t)v * dvs + site) * 6;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -314,6 +316,28 @@ __global__ void __launch_bounds__(256) k_norm_partials(const IO *__restrict__ ba
     if (threadIdx.x == 0) partials[(int64_t)v * gridDim.x + blockIdx.x] = red[0];
 }
 
+// Copies the interleaved records of one x'-row (hx sites starting at site r of
+// block b, all rec_n vectors) between global memory and a shared-memory row
+// of the same layout (colour planes hx * rec_n elements apart), 16 bytes per
+// thread and step.  to_smem selects the direction.
+template <int VP>
+__device__ __forceinline__ void row_copy(unsigned char *smr, const void *gbase, int b, int r, const SubGeom &g, int hx,
+                                         int rec_n, bool to_smem)
+{
+    constexpr int SB = VRec<VP>::SB;
+    const int segB = hx * rec_n * SB;  // one colour (or the whole row for 16-bit records)
+    const int nseg = il_planes(VP) ? 3 : 1;
+    char *blk = (char *)gbase + (int64_t)b * g.Ps * rec_n * vfmt_bytes(VP);
+    for (int c = 0; c < nseg; ++c) {
+        uint4 *gs = reinterpret_cast<uint4 *>(blk + ((int64_t)c * g.Ps + r) * rec_n * SB);
+        uint4 *ss = reinterpret_cast<uint4 *>(smr + c * segB);
+        if (to_smem)
+            for (int k = threadIdx.x; k < segB / 16; k += blockDim.x) ss[k] = gs[k];
+        else
+            for (int k = threadIdx.x; k < segB / 16; k += blockDim.x) gs[k] = ss[k];
+    }
+}
+
 // Row transposes between the canonical layout and the interleaved records.
 // One CTA per canonical x-row (t, z, y): the row's Lx sites are two x'-rows
 // of hx records groups in sublattices (x even) and (x odd), each a contiguous
@@ -334,19 +358,15 @@ __global__ void __launch_bounds__(256) k_unpack_rows(const char *__restrict__ sr
     const int r = ((z >> 1) * g.hy + (y >> 1)) * hx;
     const int segB = hx * rec_n * VBY;
     // stage both x'-rows (all rec_n records) with 16-byte loads
-    for (int par = 0; par < 2; ++par) {
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + (((int64_t)(ts * 8 + (sub0 | par)) * g.Ps + r) * rec_n) * VBY);
-        uint4 *d4 = reinterpret_cast<uint4 *>(smr + par * segB);
-        for (int k = threadIdx.x; k < segB / 16; k += blockDim.x) d4[k] = s4[k];
-    }
+    for (int par = 0; par < 2; ++par) row_copy<VP>(smr + par * segB, src, ts * 8 + (sub0 | par), r, g, hx, rec_n, true);
     __syncthreads();
     typedef typename VRec<VP>::R R;
     const int64_t site0 = (((int64_t)(t_first + ts) * Lz + z) * Ly + y) * Lx;
     for (int k = threadIdx.x; k < nvec * Lx; k += blockDim.x) {
         const int v = k / Lx, x = k - v * Lx;
         cpx<R> val[3];
-        VRec<VP>::load(reinterpret_cast<const char *>(smr) + (x & 1) * segB + (x >> 1) * rec_n * VBY, rec_n, rec_v0 + v,
-                       val);
+        VRec<VP>::load(reinterpret_cast<const char *>(smr) + (x & 1) * segB + (x >> 1) * rec_n * VRec<VP>::SB, hx * rec_n,
+                       rec_v0 + v, val);
         IO *p = dst + ((int64_t)v * dvs + site0 + x) * 6;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -371,11 +391,8 @@ __global__ void __launch_bounds__(256) k_pack_rows(const IO *__restrict__ src, i
     const int segB = hx * rec_n * VBY;
     const bool partial = nvec != rec_n;
     if (partial) {  // keep the records of the other slots: start from the current segments
-        for (int par = 0; par < 2; ++par) {
-            const uint4 *s4 = reinterpret_cast<const uint4 *>(dst + (((int64_t)(ts * 8 + (sub0 | par)) * g.Ps + r) * rec_n) * VBY);
-            uint4 *d4 = reinterpret_cast<uint4 *>(smr + par * segB);
-            for (int k = threadIdx.x; k < segB / 16; k += blockDim.x) d4[k] = s4[k];
-        }
+        for (int par = 0; par < 2; ++par)
+            row_copy<VP>(smr + par * segB, dst, ts * 8 + (sub0 | par), r, g, hx, rec_n, true);
         __syncthreads();
     }
     typedef typename VRec<VP>::R R;
@@ -389,15 +406,12 @@ __global__ void __launch_bounds__(256) k_pack_rows(const IO *__restrict__ src, i
             val[c].re = (R)p[2 * c];
             val[c].im = (R)p[2 * c + 1];
         }
-        VRec<VP>::store(reinterpret_cast<char *>(smr) + (x & 1) * segB + (x >> 1) * rec_n * VBY, rec_n, rec_v0 + v,
-                        val);
+        VRec<VP>::store(reinterpret_cast<char *>(smr) + (x & 1) * segB + (x >> 1) * rec_n * VRec<VP>::SB, hx * rec_n,
+                        rec_v0 + v, val);
     }
     __syncthreads();
-    for (int par = 0; par < 2; ++par) {
-        uint4 *d4 = reinterpret_cast<uint4 *>(dst + (((int64_t)(ts * 8 + (sub0 | par)) * g.Ps + r) * rec_n) * VBY);
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(smr + par * segB);
-        for (int k = threadIdx.x; k < segB / 16; k += blockDim.x) d4[k] = s4[k];
-    }
+    for (int par = 0; par < 2; ++par)
+        row_copy<VP>(smr + par * segB, dst, ts * 8 + (sub0 | par), r, g, hx, rec_n, false);
 }
 
 inline int spb_of(int nvec) { return std::max(1, 256 / nvec); }
@@ -576,8 +590,10 @@ static cudaError_t unpack_il_io(const char *src, int prec, IO *dst, int64_t dvs,
 
 bool rows_transpose_ok(const SubGeom &g, int rec_n, int prec, const int L[4])
 {
-    const int segB = g.hx * rec_n * vfmt_bytes(prec);
-    return segB % 16 == 0 && 2 * segB <= 48 * 1024 && (int64_t)L[1] * L[2] <= 0x7fffffff;
+    // each colour plane's (or the 16-bit row's) segment is copied in 16-byte words
+    const int colB = g.hx * rec_n * il_site_bytes(prec);
+    const int rowB = g.hx * rec_n * vfmt_bytes(prec);
+    return colB % 16 == 0 && 2 * rowB <= 48 * 1024 && (int64_t)L[1] * L[2] <= 0x7fffffff;
 }
 
 template <typename IO>

@@ -135,6 +135,11 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
     const int64_t recB = (int64_t)nvec * VBY;  // bytes of one site's records
     const char *inblk = in + (int64_t)blk * g.Ps * recB;
     char *outblk = out + (int64_t)blk * g.Ps * recB;
+    // interleaved layout: site stride nvec * SB; F32 / F64 colour planes cs apart
+    constexpr int SB = VRec<VP>::SB;
+    constexpr bool PL = il_planes(VP);
+    const int64_t sst = (int64_t)nvec * SB;
+    const int cs_g = g.Ps * nvec, cs_s = hx * nvec;  // colour stride in global memory / in a staged row
 
     const int tx = nvec / VB;
     const int tid = threadIdx.x;
@@ -160,6 +165,17 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
     };
     const unsigned wrow_bytes = (unsigned)(hx * WB);
     const unsigned row_bytes = (unsigned)pl.rowB;
+    // psi row starting at site r0 into a row slot: one segment per colour plane
+    auto load_prow = [&](char *dst, int r0, uint64_t *bar) {
+        if constexpr (PL) {
+            const unsigned segB = (unsigned)(hx * nvec * SB);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                bulk_load(dst + c * segB, inblk + ((int64_t)c * g.Ps + r0) * sst, segB, bar);
+        } else {
+            bulk_load(dst, inblk + (int64_t)r0 * sst, row_bytes, bar);
+        }
+    };
 
     // Stage r (r >= 0): psi row r+1 of this plane, rows r of planes z-1, z+1,
     // W rows r (3 dirs), W_z row r of plane z-1.
@@ -167,9 +183,9 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
         uint64_t *bar = &bars[r & 1];
         const int y = r, yn = wrap_y(r + 1);
         mbar_expect_tx(bar, 3 * row_bytes + 4 * wrow_bytes);
-        bulk_load(Y + ring4(r + 1) * rowS, inblk + (int64_t)row_of(zq, yn) * recB, row_bytes, bar);
-        bulk_load(Z + ((r & 1) * 2 + 0) * rowS, inblk + (int64_t)row_of(zm, y) * recB, row_bytes, bar);
-        bulk_load(Z + ((r & 1) * 2 + 1) * rowS, inblk + (int64_t)row_of(zp, y) * recB, row_bytes, bar);
+        load_prow(Y + ring4(r + 1) * rowS, row_of(zq, yn), bar);
+        load_prow(Z + ((r & 1) * 2 + 0) * rowS, row_of(zm, y), bar);
+        load_prow(Z + ((r & 1) * 2 + 1) * rowS, row_of(zp, y), bar);
 #pragma unroll
         for (int d = 0; d < 3; ++d) load_wrow(Wc + (ring3(r) * 3 + d) * wS, d, row_of(zq, y), bar);
         load_wrow(Wz + (r & 1) * wS, 2, row_of(zm, y), bar);
@@ -194,8 +210,8 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
     if (tid == 0) {
         uint64_t *bar = &full[1];
         mbar_expect_tx(bar, 2 * row_bytes + 3 * wrow_bytes);
-        bulk_load(Y + ring4(-1) * rowS, inblk + (int64_t)row_of(zq, hy - 1) * recB, row_bytes, bar);
-        bulk_load(Y + ring4(0) * rowS, inblk + (int64_t)row_of(zq, 0) * recB, row_bytes, bar);
+        load_prow(Y + ring4(-1) * rowS, row_of(zq, hy - 1), bar);
+        load_prow(Y + ring4(0) * rowS, row_of(zq, 0), bar);
 #pragma unroll
         for (int d = 0; d < 3; ++d) load_wrow(Wc + (ring3(-1) * 3 + d) * wS, d, row_of(zq, hy - 1), bar);
         issue_stage(0);
@@ -236,7 +252,7 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
             const char *Wrow = Wc + ring3(y) * 3 * wS;
             const char *Wym = Wc + (ring3(y - 1) * 3 + 1) * wS;
             const char *Wzm = Wz + (y & 1) * wS;
-            const unsigned rs = (unsigned)recB;
+            const unsigned rs = (unsigned)sst;
             // Operand addresses of the six hops, in the order of site_step:
             // x forward, x backward, y forward, y backward, z forward, z backward.
             const char *wsrc[6] = {Wrow, Wrow, Wrow + wS, Wym, Wrow + 2 * wS, Wzm};
@@ -251,12 +267,12 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
             // software pipeline: the operands of hop h+1 are loaded before hop h is applied
             cpx<R> m[2][9], p[2][VB][3];
             WFmt<WF>::load(wsrc[0], hx, wsite[0], m[0]);
-            RecGroup<VP, VB>::load(psrc[0], nvec, t, T, p[0]);
+            RecGroup<VP, VB, false>::load(psrc[0], cs_s, t, T, p[0]);
 #pragma unroll
             for (int h = 0; h < 6; ++h) {
                 if (h + 1 < 6) {
                     WFmt<WF>::load(wsrc[h + 1], hx, wsite[h + 1], m[(h + 1) & 1]);
-                    RecGroup<VP, VB>::load(psrc[h + 1], nvec, t, T, p[(h + 1) & 1]);
+                    RecGroup<VP, VB, false>::load(psrc[h + 1], cs_s, t, T, p[(h + 1) & 1]);
                 }
 #pragma unroll
                 for (int k = 0; k < VB; ++k) {
@@ -267,7 +283,7 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
                 }
             }
             cpx<R> c[VB][3], o[VB][3];
-            RecGroup<VP, VB>::load(Yc + xq * rs, nvec, t, T, c);
+            RecGroup<VP, VB, false>::load(Yc + xq * rs, cs_s, t, T, c);
 #pragma unroll
             for (int k = 0; k < VB; ++k) {
                 const R a = a_v[k];
@@ -277,7 +293,7 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
                     o[k][q].im = fma(a, fma(R(-6), c[k][q].im, acc[k][q].im), c[k][q].im);
                 }
             }
-            RecGroup<VP, VB>::store(outblk + ((int64_t)row_of(zq, y) + xq) * recB, nvec, t, T, o);
+            RecGroup<VP, VB>::store(outblk + ((int64_t)row_of(zq, y) + xq) * sst, cs_g, t, T, o);
                 }
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[y & 1]);

@@ -179,7 +179,8 @@ __device__ __forceinline__ void step_il_body(const char *__restrict__ W, const c
     // record group of site s of this block at rin + s * nvec * VBY
     const char *rin = in + (int64_t)blk * g.Ps * nvec * VBY;
     char *rout = out + (int64_t)blk * g.Ps * nvec * VBY;
-    const unsigned rstride = (unsigned)nvec * VBY;
+    const unsigned rstride = (unsigned)nvec * VRec<VP>::SB;  // site stride
+    const int cs = g.Ps * nvec;                                    // colour planes
     cpx<R> acc[VB][3];
 #pragma unroll
     for (int k = 0; k < VB; ++k)
@@ -189,16 +190,16 @@ __device__ __forceinline__ void step_il_body(const char *__restrict__ W, const c
     for (int d = 0; d < 3; ++d) {
         cpx<R> m[9], p[VB][3];
         WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, i, m);
-        RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, nvec, t, T, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, cs, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
         WFmt<WF>::load(wb + d * g.Ps * WB, g.Ps, bw[d], m);
-        RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, nvec, t, T, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, cs, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
     }
     cpx<R> c[VB][3], o[VB][3];
-    RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, nvec, t, T, c);
+    RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, cs, t, T, c);
 #pragma unroll
     for (int k = 0; k < VB; ++k) {
         const R a = (R)alpha[il_vec<VP, VB>(t, T, k)];
@@ -218,11 +219,11 @@ __device__ __forceinline__ void step_il_body(const char *__restrict__ W, const c
             for (int k = 0; k < VB; ++k) all = all && on[k];
             return all;
         }())) {
-        RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, nvec, t, T, o);
+        RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, cs, t, T, o);
     } else {
 #pragma unroll
         for (int k = 0; k < VB; ++k)
-            if (on[k]) VRec<VP>::store(rout + (unsigned)i * rstride, nvec, il_vec<VP, VB>(t, T, k), o[k]);
+            if (on[k]) VRec<VP>::store(rout + (unsigned)i * rstride, cs, il_vec<VP, VB>(t, T, k), o[k]);
     }
 }
 
@@ -242,6 +243,17 @@ __global__ void __launch_bounds__(128, 8) k_step_il_occ(const char *__restrict__
                                                         const int *__restrict__ active, SubGeom g, int nvec)
 {
     step_il_body<VP, WF, VB>(W, in, out, alpha, active, g, nvec);
+}
+
+// alpha of vector v in the arithmetic precision: FP32 kernels read the copy
+// rounded to FP32 beforehand (the same value as converting the FP64 one).
+template <typename R>
+__device__ __forceinline__ R alpha_of(const double *__restrict__ alpha, const float *__restrict__ alphaf, int v)
+{
+    if constexpr (sizeof(R) == 4)
+        return alphaf[v];
+    else
+        return (R)alpha[v];
 }
 
 // Packed FP32 pair forms of mv_add / mdv_add for VB vectors: every (re, im)
@@ -310,7 +322,7 @@ __device__ __forceinline__ void mdv_add_x2(const cpx<float> m[9], const cpx<floa
 template <int VP, int WF, int VB, bool PK>
 __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, const char *__restrict__ in,
                                                   char *__restrict__ out, const double *__restrict__ alpha,
-                                                  SubGeom g, int nvec)
+                                                  const float *__restrict__ alphaf, SubGeom g, int nvec)
 {
     typedef typename VRec<VP>::R R;
     constexpr int WB = wfmt_bytes(WF);
@@ -378,7 +390,8 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
     bw[2] = zq == 0 ? i + (g.hz - 1) * sz : i - sz;
     const char *rin = in + (int64_t)blk * g.Ps * nvec * VBY;
     char *rout = out + (int64_t)blk * g.Ps * nvec * VBY;
-    const unsigned rstride = (unsigned)nvec * VBY;
+    const unsigned rstride = (unsigned)nvec * VRec<VP>::SB;  // site stride
+    const int cs = g.Ps * nvec;                                    // colour planes
     const char *ws = reinterpret_cast<const char *>(wsm);
     cpx<R> c[VB][3], o[VB][3];
     if constexpr (PK) {
@@ -392,17 +405,17 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
         for (int d = 0; d < 3; ++d) {
             cpx<float> m[9], p[VB][3];
             WFmt<WF>::load(ws + (2 * d) * setB, spb, k, m);
-            RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, nvec, t, T, p);
+            RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, cs, t, T, p);
             mv_add_x2<VB>(m, p, acc);
             WFmt<WF>::load(ws + (2 * d + 1) * setB, spb, k, m);
-            RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, nvec, t, T, p);
+            RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, cs, t, T, p);
             mdv_add_x2<VB>(m, p, acc);
         }
-        RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, nvec, t, T, c);
+        RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, cs, t, T, c);
         const float2 m6 = make_float2(-6.f, -6.f);
 #pragma unroll
         for (int kk = 0; kk < VB; ++kk) {
-            const float a = (float)alpha[il_vec<VP, VB>(t, T, kk)];
+            const float a = alphaf[il_vec<VP, VB>(t, T, kk)];
             const float2 a2 = make_float2(a, a);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -422,18 +435,18 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
         for (int d = 0; d < 3; ++d) {
             cpx<R> m[9], p[VB][3];
             WFmt<WF>::load(ws + (2 * d) * setB, spb, k, m);
-            RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, nvec, t, T, p);
+            RecGroup<VP, VB>::load(rin + (unsigned)fw[d] * rstride, cs, t, T, p);
 #pragma unroll
             for (int kk = 0; kk < VB; ++kk) mv_add(m, p[kk], acc[kk]);
             WFmt<WF>::load(ws + (2 * d + 1) * setB, spb, k, m);
-            RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, nvec, t, T, p);
+            RecGroup<VP, VB>::load(rin + (unsigned)bw[d] * rstride, cs, t, T, p);
 #pragma unroll
             for (int kk = 0; kk < VB; ++kk) mdv_add(m, p[kk], acc[kk]);
         }
-        RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, nvec, t, T, c);
+        RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, cs, t, T, c);
 #pragma unroll
         for (int kk = 0; kk < VB; ++kk) {
-            const R a = (R)alpha[il_vec<VP, VB>(t, T, kk)];
+            const R a = alpha_of<R>(alpha, alphaf, il_vec<VP, VB>(t, T, kk));
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 o[kk][q].re = fma(a, fma(R(-6), c[kk][q].re, acc[kk][q].re), c[kk][q].re);
@@ -441,7 +454,7 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
             }
         }
     }
-    RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, nvec, t, T, o);
+    RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, cs, t, T, o);
 }
 
 // --------------------------------------------------------------------------
@@ -459,7 +472,7 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
 template <int VP, int WF, int VB, bool PRE>
 __global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, const char *__restrict__ in,
                                                   char *__restrict__ out, const double *__restrict__ alpha,
-                                                  SubGeom g, int nvec)
+                                                  const float *__restrict__ alphaf, SubGeom g, int nvec)
 {
     static_assert(VP != P_F64, "packed FP32 pairs only");
     constexpr int WB = wfmt_bytes(WF);
@@ -489,14 +502,15 @@ __global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, co
     nb[6] = i;
     const char *rin = in + (int64_t)blk * g.Ps * nvec * VBY;
     char *rout = out + (int64_t)blk * g.Ps * nvec * VBY;
-    const unsigned rstride = (unsigned)nvec * VBY;
+    const unsigned rstride = (unsigned)nvec * VRec<VP>::SB;  // site stride
+    const int cs = g.Ps * nvec;                                    // colour planes
     // PRE: all seven record groups are requested before the W staging, so
     // their latencies overlap one another and the staging.
     cpx<float> pre[PRE ? 7 : 1][VB][3];
     if constexpr (PRE) {
         if (act) {
 #pragma unroll
-            for (int q = 0; q < 7; ++q) RecGroup<VP, VB>::load(rin + (unsigned)nb[q] * rstride, nvec, t, T, pre[q]);
+            for (int q = 0; q < 7; ++q) RecGroup<VP, VB>::load(rin + (unsigned)nb[q] * rstride, cs, t, T, pre[q]);
         }
     }
     {
@@ -541,7 +555,7 @@ __global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, co
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
         cpx<float> pl[VB][3];
-        if constexpr (!PRE) RecGroup<VP, VB>::load(rin + (unsigned)nb[q] * rstride, nvec, t, T, pl);
+        if constexpr (!PRE) RecGroup<VP, VB>::load(rin + (unsigned)nb[q] * rstride, cs, t, T, pl);
         const float4 *wq = wpk + q * 9 * spb + k;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -575,12 +589,12 @@ __global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, co
 #pragma unroll
             for (int r = 0; r < 3; ++r) cc[v][r] = pre[6 % (PRE ? 7 : 1)][v][r];
     } else {
-        RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, nvec, t, T, cc);
+        RecGroup<VP, VB>::load(rin + (unsigned)i * rstride, cs, t, T, cc);
     }
     const float2 m6 = make_float2(-6.f, -6.f);
 #pragma unroll
     for (int v = 0; v < VB; ++v) {
-        const float a = (float)alpha[il_vec<VP, VB>(t, T, v)];
+        const float a = alphaf[il_vec<VP, VB>(t, T, v)];
         const float2 a2 = make_float2(a, a);
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -590,7 +604,7 @@ __global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, co
             o[v][r].im = u.y;
         }
     }
-    RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, nvec, t, T, o);
+    RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, cs, t, T, o);
 }
 
 // --------------------------------------------------------------------------
@@ -623,7 +637,8 @@ __global__ void __launch_bounds__(256) k_step_zm(const char *__restrict__ W, con
     const char *wb = W + (int64_t)blk * 3 * g.Ps * WB;
     const char *rin = in + (int64_t)blk * g.Ps * nvec * VBY;
     char *rout = out + (int64_t)blk * g.Ps * nvec * VBY;
-    const unsigned rstride = (unsigned)nvec * VBY;
+    const unsigned rstride = (unsigned)nvec * VRec<VP>::SB;  // site stride
+    const int cs = g.Ps * nvec;                                    // colour planes
     R a_v[VB];
 #pragma unroll
     for (int k = 0; k < VB; ++k) a_v[k] = (R)alpha[il_vec<VP, VB>(t, T, k)];
@@ -631,15 +646,15 @@ __global__ void __launch_bounds__(256) k_step_zm(const char *__restrict__ W, con
     auto site = [&](int z) { return z * sz + col; };
     // column state: psi(z-1), psi(z), psi(z+1) and W_z(z-1)
     cpx<R> pm[VB][3], pc[VB][3], pp[VB][3], wzm[9];
-    RecGroup<VP, VB>::load(rin + (unsigned)site(hz - 1) * rstride, nvec, t, T, pm);
-    RecGroup<VP, VB>::load(rin + (unsigned)site(0) * rstride, nvec, t, T, pc);
-    RecGroup<VP, VB>::load(rin + (unsigned)site(1 % hz) * rstride, nvec, t, T, pp);
+    RecGroup<VP, VB>::load(rin + (unsigned)site(hz - 1) * rstride, cs, t, T, pm);
+    RecGroup<VP, VB>::load(rin + (unsigned)site(0) * rstride, cs, t, T, pc);
+    RecGroup<VP, VB>::load(rin + (unsigned)site(1 % hz) * rstride, cs, t, T, pp);
     WFmt<WF>::load(wb + 2 * g.Ps * WB, g.Ps, site(hz - 1), wzm);
     for (int z = 0; z < hz; ++z) {
         const int i = site(z);
         const int zn = (z + 2) % hz;
         cpx<R> pn[VB][3];  // psi(z+2): next iteration's psi(z+1)
-        RecGroup<VP, VB>::load(rin + (unsigned)site(zn) * rstride, nvec, t, T, pn);
+        RecGroup<VP, VB>::load(rin + (unsigned)site(zn) * rstride, cs, t, T, pn);
         cpx<R> acc[VB][3];
 #pragma unroll
         for (int k = 0; k < VB; ++k)
@@ -648,20 +663,20 @@ __global__ void __launch_bounds__(256) k_step_zm(const char *__restrict__ W, con
         cpx<R> m[9], p[VB][3], wz[9];
         // x forward / backward
         WFmt<WF>::load(wb, g.Ps, i, m);
-        RecGroup<VP, VB>::load(rin + (unsigned)(i - xq + xp) * rstride, nvec, t, T, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)(i - xq + xp) * rstride, cs, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
         WFmt<WF>::load(wb, g.Ps, i - xq + xm, m);
-        RecGroup<VP, VB>::load(rin + (unsigned)(i - xq + xm) * rstride, nvec, t, T, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)(i - xq + xm) * rstride, cs, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
         // y forward / backward
         WFmt<WF>::load(wb + g.Ps * WB, g.Ps, i, m);
-        RecGroup<VP, VB>::load(rin + (unsigned)(i + (yp - yq) * sy) * rstride, nvec, t, T, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)(i + (yp - yq) * sy) * rstride, cs, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mv_add(m, p[k], acc[k]);
         WFmt<WF>::load(wb + g.Ps * WB, g.Ps, i + (ym - yq) * sy, m);
-        RecGroup<VP, VB>::load(rin + (unsigned)(i + (ym - yq) * sy) * rstride, nvec, t, T, p);
+        RecGroup<VP, VB>::load(rin + (unsigned)(i + (ym - yq) * sy) * rstride, cs, t, T, p);
 #pragma unroll
         for (int k = 0; k < VB; ++k) mdv_add(m, p[k], acc[k]);
         // z forward (W_z(z), psi(z+1)) / backward (W_z(z-1), psi(z-1)), from registers
@@ -680,7 +695,7 @@ __global__ void __launch_bounds__(256) k_step_zm(const char *__restrict__ W, con
                 o[k][q].im = fma(a, fma(R(-6), pc[k][q].im, acc[k][q].im), pc[k][q].im);
             }
         }
-        RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, nvec, t, T, o);
+        RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, cs, t, T, o);
         // slide the column window
 #pragma unroll
         for (int k = 0; k < VB; ++k)
@@ -862,8 +877,8 @@ template <int VP, int WF, int VB> cudaError_t step_il_launch(const StepArgs &a)
     int spb = a.tile[0] > 0 ? a.tile[0] : il_spb(tx, occ ? 128 : a.threads);
     spb = std::max(1, std::min(spb, cap / tx));
     spb = std::min(spb, a.g.hx);  // a strip never spans more than one row
-    const bool packed = (a.tile[1] == 2 || a.tile[1] == 3) && a.active == nullptr && VP != P_F64;
-    const bool staged = a.tile[1] > 0 && a.active == nullptr;
+    const bool packed = (a.tile[1] == 2 || a.tile[1] == 3) && a.active == nullptr && a.alphaf && VP != P_F64;
+    const bool staged = a.tile[1] > 0 && a.active == nullptr && a.alphaf;
     constexpr int kPackB = 6 * 9 * 16;  // W packs per site of the packed kernel
     // shared memory within the default dynamic limit (48 KB)
     if (packed)
@@ -878,20 +893,20 @@ template <int VP, int WF, int VB> cudaError_t step_il_launch(const StepArgs &a)
         // packed FP32 pairs with W packs in shared memory; 3 = all records requested up front
         if constexpr (VP != P_F64) {
             if (a.tile[1] == 3)
-                k_step_ilx<VP, WF, VB, true><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g,
-                                                                                      a.nvec);
+                k_step_ilx<VP, WF, VB, true><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha,
+                                                                                      a.alphaf, a.g, a.nvec);
             else
                 k_step_ilx<VP, WF, VB, false><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha,
-                                                                                       a.g, a.nvec);
+                                                                                       a.alphaf, a.g, a.nvec);
         }
-    } else if (a.tile[1] == 4 && a.active == nullptr && VP != P_F64) {
+    } else if (staged && a.tile[1] == 4 && VP != P_F64) {
         // W of the strip staged in shared memory as stored, packed FP32 pair FMAs
         if constexpr (VP != P_F64)
             k_step_ilw<VP, WF, VB, true><<<grid, block, 6 * ((spb * wfmt_bytes(WF) + 15) / 16 * 16), a.stream>>>(
-                a.W, a.in, a.out, a.alpha, a.g, a.nvec);
-    } else if (a.tile[1] > 0 && a.active == nullptr)  // W of the strip staged in shared memory
+                a.W, a.in, a.out, a.alpha, a.alphaf, a.g, a.nvec);
+    } else if (staged)  // W of the strip staged in shared memory
         k_step_ilw<VP, WF, VB, false><<<grid, block, 6 * ((spb * wfmt_bytes(WF) + 15) / 16 * 16), a.stream>>>(
-            a.W, a.in, a.out, a.alpha, a.g, a.nvec);
+            a.W, a.in, a.out, a.alpha, a.alphaf, a.g, a.nvec);
     else if (occ)
         k_step_il_occ<VP, WF, VB><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g,
                                                                      a.nvec);

@@ -393,127 +393,189 @@ template <> struct VFmt<P_F16> : VFmtH<__half> {};
 template <> struct VFmt<P_BF16> : VFmtH<__nv_bfloat16> {};
 
 // --------------------------------------------------------------------------
-// Interleaved (vector-innermost) records.  The nvec vectors of one site form
-// one contiguous record group of nvec * bytes at (block * Ps + i) * nvec * bytes:
-//   F64 / F32: colour-major, [colour][vector] complex numbers (double2 /
-//              float2), so colour c of vectors w, w+1, ... is contiguous;
-//   16-bit   : one 16-byte record per vector {3 x half2, float scale}.
-// A warp covers consecutive (site, vector) pairs and the W of a site is one
-// broadcast for all its lanes.  A thread that owns VB vectors of a site takes
-// the load units t, t + T, t + 2T, ... (T = nvec / VB threads per site), a
-// unit being the vectors whose colour c fills one 16-byte word (two for F32,
-// one otherwise).  Consecutive threads then read consecutive 16-byte words:
-// every warp load and store covers whole 32-byte sectors.
+// Interleaved (vector-innermost) records, per (slice, sublattice) block of
+// Ps sites and nvec vectors:
+//   F64 / F32: three colour planes; plane c holds, for every site i, the nvec
+//              complex numbers (double2 / float2) of colour c contiguously:
+//              element (c, i, v) at ((c * Ps + i) * nvec + v) * 16 / 8 bytes
+//              from the block, so colour c of consecutive sites is contiguous;
+//   16-bit   : one 16-byte record per (site, vector) {3 x half2, float scale}
+//              at (i * nvec + v) * 16 bytes.
+// The block occupies Ps * nvec * vfmt_bytes bytes either way.  A site pointer
+// is block + i * nvec * SB; colour planes are cs = Ps * nvec elements apart.
+// A thread that owns VB vectors of a site reads vector units t, t + T, ...
+// (T = nvec / VB threads per site), a unit being what one 16-byte word holds
+// per colour (two F32 vectors, one otherwise); F32 threads with VB = 4 own the
+// adjacent units 2t, 2t+1 and read them with one 32-byte load.  Consecutive
+// lanes read consecutive words, across site boundaries too.
 // --------------------------------------------------------------------------
 template <int P> struct VRec;
 
 template <> struct VRec<P_F64> {
     typedef double R;
-    static constexpr int U = 1;
-    // vector w of the group at grp (n vectors)
-    static __device__ __forceinline__ void load(const char *grp, int n, int w, cpx<double> v[3])
+    static constexpr int U = 1;   // vectors per 16-byte unit of one colour
+    static constexpr int SB = 16; // site stride per vector (bytes)
+    static __device__ __forceinline__ void load(const char *s, int cs, int w, cpx<double> v[3])
     {
-        const double2 *p = reinterpret_cast<const double2 *>(grp) + w;
+        const double2 *p = reinterpret_cast<const double2 *>(s) + w;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            double2 a = p[c * n];
+            double2 a = p[c * cs];
             v[c].re = a.x;
             v[c].im = a.y;
         }
     }
-    static __device__ __forceinline__ void store(char *grp, int n, int w, const cpx<double> v[3])
+    static __device__ __forceinline__ void store(char *s, int cs, int w, const cpx<double> v[3])
     {
-        double2 *p = reinterpret_cast<double2 *>(grp) + w;
+        double2 *p = reinterpret_cast<double2 *>(s) + w;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p[c * n] = make_double2(v[c].re, v[c].im);
+        for (int c = 0; c < 3; ++c) p[c * cs] = make_double2(v[c].re, v[c].im);
     }
 };
 
 template <> struct VRec<P_F32> {
     typedef float R;
     static constexpr int U = 2;
-    static __device__ __forceinline__ void load(const char *grp, int n, int w, cpx<float> v[3])
+    static constexpr int SB = 8;
+    static __device__ __forceinline__ void load(const char *s, int cs, int w, cpx<float> v[3])
     {
-        const float2 *p = reinterpret_cast<const float2 *>(grp) + w;
+        const float2 *p = reinterpret_cast<const float2 *>(s) + w;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float2 a = p[c * n];
+            float2 a = p[c * cs];
             v[c].re = a.x;
             v[c].im = a.y;
         }
     }
-    static __device__ __forceinline__ void store(char *grp, int n, int w, const cpx<float> v[3])
+    static __device__ __forceinline__ void store(char *s, int cs, int w, const cpx<float> v[3])
     {
-        float2 *p = reinterpret_cast<float2 *>(grp) + w;
+        float2 *p = reinterpret_cast<float2 *>(s) + w;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p[c * n] = make_float2(v[c].re, v[c].im);
+        for (int c = 0; c < 3; ++c) p[c * cs] = make_float2(v[c].re, v[c].im);
     }
-    // the unit of vectors 2u, 2u+1 (n even): one 16-byte word per colour
-    static __device__ __forceinline__ void load2(const char *grp, int n, int u, cpx<float> a[3], cpx<float> b[3])
+    // unit u = vectors 2u, 2u+1: one 16-byte word per colour
+    static __device__ __forceinline__ void load2(const char *s, int cs, int u, cpx<float> a[3], cpx<float> b[3])
     {
-        const float4 *p = reinterpret_cast<const float4 *>(grp) + u;
+        const float4 *p = reinterpret_cast<const float4 *>(s) + u;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float4 q = p[c * (n >> 1)];
+            float4 q = p[c * (cs >> 1)];
             a[c].re = q.x;
             a[c].im = q.y;
             b[c].re = q.z;
             b[c].im = q.w;
         }
     }
-    static __device__ __forceinline__ void store2(char *grp, int n, int u, const cpx<float> a[3], const cpx<float> b[3])
+    static __device__ __forceinline__ void store2(char *s, int cs, int u, const cpx<float> a[3], const cpx<float> b[3])
     {
-        float4 *p = reinterpret_cast<float4 *>(grp) + u;
+        float4 *p = reinterpret_cast<float4 *>(s) + u;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p[c * (n >> 1)] = make_float4(a[c].re, a[c].im, b[c].re, b[c].im);
+        for (int c = 0; c < 3; ++c) p[c * (cs >> 1)] = make_float4(a[c].re, a[c].im, b[c].re, b[c].im);
+    }
+    // units 2u2, 2u2+1 = vectors 4u2 .. 4u2+3: one 32-byte global load / store per colour
+    static __device__ __forceinline__ void load4g(const char *s, int cs, int u2, cpx<float> v[4][3])
+    {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float *p = reinterpret_cast<const float *>(s) + 2 * ((int64_t)c * cs + 4 * u2);
+            float f[8];
+            asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]),
+                           "=f"(f[7])
+                         : "l"(p));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[k][c].re = f[2 * k];
+                v[k][c].im = f[2 * k + 1];
+            }
+        }
+    }
+    static __device__ __forceinline__ void store4g(char *s, int cs, int u2, const cpx<float> v[4][3])
+    {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float *p = reinterpret_cast<float *>(s) + 2 * ((int64_t)c * cs + 4 * u2);
+            asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0][c].re),
+                         "f"(v[0][c].im), "f"(v[1][c].re), "f"(v[1][c].im), "f"(v[2][c].re), "f"(v[2][c].im),
+                         "f"(v[3][c].re), "f"(v[3][c].im)
+                         : "memory");
+        }
     }
 };
 
 template <typename H> struct VRecH {
     typedef float R;
     static constexpr int U = 1;
-    static __device__ __forceinline__ void load(const char *grp, int, int w, cpx<float> v[3])
+    static constexpr int SB = 16;
+    static __device__ __forceinline__ void load(const char *s, int, int w, cpx<float> v[3])
     {
-        VFmtH<H>::template load<false>(grp, 0, w, v);
+        VFmtH<H>::template load<false>(s, 0, w, v);
     }
-    static __device__ __forceinline__ void store(char *grp, int, int w, const cpx<float> v[3])
+    static __device__ __forceinline__ void store(char *s, int, int w, const cpx<float> v[3])
     {
-        VFmtH<H>::template store<false>(grp, 0, w, v);
+        VFmtH<H>::template store<false>(s, 0, w, v);
     }
 };
 template <> struct VRec<P_F16> : VRecH<__half> {};
 template <> struct VRec<P_BF16> : VRecH<__nv_bfloat16> {};
 
+// Bytes between consecutive sites' records in the interleaved layout, per vector.
+__host__ __device__ constexpr int il_site_bytes(int prec) { return prec == P_F64 ? 16 : prec == P_F32 ? 8 : 16; }
+// Whether the interleaved layout splits colours into planes.
+__host__ __device__ constexpr bool il_planes(int prec) { return prec == P_F64 || prec == P_F32; }
+
+// F32 threads with four vectors own adjacent units.
+template <int VP, int VB> __host__ __device__ constexpr bool il_adj4() { return VP == P_F32 && VB == 4; }
+
 // Vector index of the k-th of the VB vectors that thread t (of T = nvec / VB
 // per site) owns.
 template <int VP, int VB> __device__ __forceinline__ int il_vec(int t, int T, int k)
 {
-    constexpr int U = VB % VRec<VP>::U == 0 ? VRec<VP>::U : 1;
-    return (t + (k / U) * T) * U + k % U;
+    if constexpr (il_adj4<VP, VB>()) {
+        return 4 * t + k;
+    } else {
+        constexpr int U = VB % VRec<VP>::U == 0 ? VRec<VP>::U : 1;
+        return (t + (k / U) * T) * U + k % U;
+    }
 }
 
-// The VB vectors of thread t in the record group at grp (n vectors).
-template <int VP, int VB> struct RecGroup {
+// The VB vectors of thread t at site pointer s (colour planes cs elements
+// apart).  GM: s is global memory (32-byte loads allowed).
+template <int VP, int VB, bool GM = true> struct RecGroup {
     typedef typename VRec<VP>::R R;
     static constexpr bool PAIRS = VRec<VP>::U == 2 && VB % 2 == 0;
-    static __device__ __forceinline__ void load(const char *grp, int n, int t, int T, cpx<R> v[VB][3])
+    static __device__ __forceinline__ void load(const char *s, int cs, int t, int T, cpx<R> v[VB][3])
     {
-        if constexpr (PAIRS) {
+        if constexpr (il_adj4<VP, VB>()) {
+            if constexpr (GM) {
+                VRec<VP>::load4g(s, cs, t, v);
+            } else {
+                VRec<VP>::load2(s, cs, 2 * t, v[0], v[1]);
+                VRec<VP>::load2(s, cs, 2 * t + 1, v[2], v[3]);
+            }
+        } else if constexpr (PAIRS) {
 #pragma unroll
-            for (int j = 0; j < VB / 2; ++j) VRec<VP>::load2(grp, n, t + j * T, v[2 * j], v[2 * j + 1]);
+            for (int j = 0; j < VB / 2; ++j) VRec<VP>::load2(s, cs, t + j * T, v[2 * j], v[2 * j + 1]);
         } else {
 #pragma unroll
-            for (int k = 0; k < VB; ++k) VRec<VP>::load(grp, n, t + k * T, v[k]);
+            for (int k = 0; k < VB; ++k) VRec<VP>::load(s, cs, t + k * T, v[k]);
         }
     }
-    static __device__ __forceinline__ void store(char *grp, int n, int t, int T, const cpx<R> v[VB][3])
+    static __device__ __forceinline__ void store(char *s, int cs, int t, int T, const cpx<R> v[VB][3])
     {
-        if constexpr (PAIRS) {
+        if constexpr (il_adj4<VP, VB>()) {
+            if constexpr (GM) {
+                VRec<VP>::store4g(s, cs, t, v);
+            } else {
+                VRec<VP>::store2(s, cs, 2 * t, v[0], v[1]);
+                VRec<VP>::store2(s, cs, 2 * t + 1, v[2], v[3]);
+            }
+        } else if constexpr (PAIRS) {
 #pragma unroll
-            for (int j = 0; j < VB / 2; ++j) VRec<VP>::store2(grp, n, t + j * T, v[2 * j], v[2 * j + 1]);
+            for (int j = 0; j < VB / 2; ++j) VRec<VP>::store2(s, cs, t + j * T, v[2 * j], v[2 * j + 1]);
         } else {
 #pragma unroll
-            for (int k = 0; k < VB; ++k) VRec<VP>::store(grp, n, t + k * T, v[k]);
+            for (int k = 0; k < VB; ++k) VRec<VP>::store(s, cs, t + k * T, v[k]);
         }
     }
 };

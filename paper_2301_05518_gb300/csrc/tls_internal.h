@@ -14,6 +14,7 @@ struct StepArgs {
     const char *in;        // packed vectors: vector v at in + v * vstride_in
     char *out;
     const double *alpha;   // device, per vector: width / (4 N)
+    const float *alphaf;   // device (nullable): alpha rounded to FP32, for the FP32-arithmetic kernels
     const int *active;     // device, per vector (nullable): 0 = leave this vector alone
     SubGeom g;
     int nblk;

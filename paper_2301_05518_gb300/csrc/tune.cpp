@@ -40,7 +40,6 @@ std::vector<Cand> candidates(int nvec, int storage, bool rows)
             for (int t : {128, 256})
                 if (t >= tx) {
                     c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 2, 0}});
-                    c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 3, 0}});  // records requested up front
                     c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 4, 0}});  // W as stored, packed FMAs
                 }
         if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0, {0, 0, 0}});

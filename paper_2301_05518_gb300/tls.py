@@ -268,11 +268,11 @@ def _entry(e):
 def tls_autotune(ctx, gauge: int, nvec: int, storage: int, timeslice: int = TLS_ALL_T, steps: int = 4):
     """Returns (best, all candidates) as dicts; the best goes to the context's table."""
     best = tls_tune_entry()
-    arr = (tls_tune_entry * 32)()
+    arr = (tls_tune_entry * 128)()
     n = ctypes.c_int()
     _check(lib.tls_autotune(ctx, int(gauge), int(nvec), int(storage), int(timeslice), int(steps),
-                            ctypes.byref(best), arr, 32, ctypes.byref(n)))
-    return _entry(best), [_entry(arr[k]) for k in range(min(n.value, 32))]
+                            ctypes.byref(best), arr, 128, ctypes.byref(n)))
+    return _entry(best), [_entry(arr[k]) for k in range(min(n.value, 128))]
 
 
 def tls_tune_set(ctx, gauge: int, nvec: int, storage: int, timeslice: int, kernel: int,
