@@ -622,7 +622,10 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         vb = 1;
         if (threads <= 0) threads = 128;
     } else if (kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS || kern == TLS_KERNEL_MRHS_ZM) {
-        if (vb <= 0 || vb > 4 || G0 % vb != 0 || (storage == TLS_F64 && vb > 2)) vb = default_il_vb(storage, G0);
+        // eight vectors per thread: FP32 storage, packed kernel (tile[1] = 2) only
+        const bool vb8 = vb == 8 && storage == TLS_F32 && tile[1] == 2 && kern == TLS_KERNEL_MRHS;
+        if (vb <= 0 || (vb > 4 && !vb8) || G0 % vb != 0 || (storage == TLS_F64 && vb > 2))
+            vb = default_il_vb(storage, G0);
         if (threads == 0) threads = 256;  // < 0: the register-capped variant
         // TMA row staging needs 16-byte copies and a row that fits in shared memory
         if (kern == TLS_KERNEL_MRHS_ROWS &&

@@ -867,7 +867,8 @@ inline int il_spb(int nvec, int threads)
     return spb;
 }
 
-template <int VP, int WF, int VB> cudaError_t step_il_launch(const StepArgs &a)
+// ONLYX: only the packed FP32 pair kernel is instantiated (eight vectors per thread).
+template <int VP, int WF, int VB, bool ONLYX = false> cudaError_t step_il_launch(const StepArgs &a)
 {
     const int tx = a.nvec / VB;
     // a strip of spb consecutive x' per CTA; tile[0] > 0 sets spb explicitly
@@ -889,6 +890,12 @@ template <int VP, int WF, int VB> cudaError_t step_il_launch(const StepArgs &a)
     dim3 block(tx, spb);
     dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    if constexpr (ONLYX) {
+        if (!packed || a.tile[1] != 2) return cudaErrorNotSupported;
+        k_step_ilx<VP, WF, VB, false><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha, a.alphaf,
+                                                                               a.g, a.nvec);
+        return cudaGetLastError();
+    } else {
     if (packed) {
         // packed FP32 pairs with W packs in shared memory; 3 = all records requested up front
         if constexpr (VP != P_F64) {
@@ -913,6 +920,7 @@ template <int VP, int WF, int VB> cudaError_t step_il_launch(const StepArgs &a)
     else
         k_step_il<VP, WF, VB><<<grid, block, 0, a.stream>>>(a.W, a.in, a.out, a.alpha, a.active, a.g, a.nvec);
     return cudaGetLastError();
+    }
 }
 
 template <int VP, int WF, int VB> cudaError_t step_zm_launch(const StepArgs &a)
@@ -967,6 +975,7 @@ template <int VP, int WF> cudaError_t step_il_w(const StepArgs &a)
             switch (vb) {
             case 2: return step_il_launch<VP, WF, 2>(a);
             case 4: return step_il_launch<VP, WF, 4>(a);
+            case 8: return step_il_launch<VP, WF, 8, true>(a);  // packed kernel only
             default: return step_il_launch<VP, WF, 1>(a);
             }
         } else if constexpr (VP == P_F64) {

@@ -524,15 +524,15 @@ __host__ __device__ constexpr int il_site_bytes(int prec) { return prec == P_F64
 // Whether the interleaved layout splits colours into planes.
 __host__ __device__ constexpr bool il_planes(int prec) { return prec == P_F64 || prec == P_F32; }
 
-// F32 threads with four vectors own adjacent units.
-template <int VP, int VB> __host__ __device__ constexpr bool il_adj4() { return VP == P_F32 && VB == 4; }
+// F32 threads with four or eight vectors own adjacent units (32-byte loads).
+template <int VP, int VB> __host__ __device__ constexpr bool il_adj4() { return VP == P_F32 && VB % 4 == 0; }
 
 // Vector index of the k-th of the VB vectors that thread t (of T = nvec / VB
 // per site) owns.
 template <int VP, int VB> __device__ __forceinline__ int il_vec(int t, int T, int k)
 {
     if constexpr (il_adj4<VP, VB>()) {
-        return 4 * t + k;
+        return VB * t + k;
     } else {
         constexpr int U = VB % VRec<VP>::U == 0 ? VRec<VP>::U : 1;
         return (t + (k / U) * T) * U + k % U;
@@ -547,11 +547,15 @@ template <int VP, int VB, bool GM = true> struct RecGroup {
     static __device__ __forceinline__ void load(const char *s, int cs, int t, int T, cpx<R> v[VB][3])
     {
         if constexpr (il_adj4<VP, VB>()) {
-            if constexpr (GM) {
-                VRec<VP>::load4g(s, cs, t, v);
-            } else {
-                VRec<VP>::load2(s, cs, 2 * t, v[0], v[1]);
-                VRec<VP>::load2(s, cs, 2 * t + 1, v[2], v[3]);
+#pragma unroll
+            for (int j = 0; j < VB / 4; ++j) {
+                const int q = VB / 4 * t + j;  // vectors 4q .. 4q+3
+                if constexpr (GM) {
+                    VRec<VP>::load4g(s, cs, q, v + 4 * j);
+                } else {
+                    VRec<VP>::load2(s, cs, 2 * q, v[4 * j], v[4 * j + 1]);
+                    VRec<VP>::load2(s, cs, 2 * q + 1, v[4 * j + 2], v[4 * j + 3]);
+                }
             }
         } else if constexpr (PAIRS) {
 #pragma unroll
@@ -564,11 +568,15 @@ template <int VP, int VB, bool GM = true> struct RecGroup {
     static __device__ __forceinline__ void store(char *s, int cs, int t, int T, const cpx<R> v[VB][3])
     {
         if constexpr (il_adj4<VP, VB>()) {
-            if constexpr (GM) {
-                VRec<VP>::store4g(s, cs, t, v);
-            } else {
-                VRec<VP>::store2(s, cs, 2 * t, v[0], v[1]);
-                VRec<VP>::store2(s, cs, 2 * t + 1, v[2], v[3]);
+#pragma unroll
+            for (int j = 0; j < VB / 4; ++j) {
+                const int q = VB / 4 * t + j;
+                if constexpr (GM) {
+                    VRec<VP>::store4g(s, cs, q, v + 4 * j);
+                } else {
+                    VRec<VP>::store2(s, cs, 2 * q, v[4 * j], v[4 * j + 1]);
+                    VRec<VP>::store2(s, cs, 2 * q + 1, v[4 * j + 2], v[4 * j + 3]);
+                }
             }
         } else if constexpr (PAIRS) {
 #pragma unroll

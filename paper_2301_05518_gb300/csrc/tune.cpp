@@ -44,6 +44,9 @@ std::vector<Cand> candidates(int nvec, int storage, bool rows)
                 }
         if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0, {0, 0, 0}});
     }
+    if (storage == TLS_F32 && G % 8 == 0)  // eight FP32 vectors per thread, packed kernel
+        for (int t : {128, 256})
+            if (t >= G / 8) c.push_back({TLS_KERNEL_MRHS, 8, t, {0, 2, 0}});
     const int vmax = storage == TLS_F64 ? 4 : 8;
     for (int vb : {1, 4, 8})
         if (vb <= vmax && (vb == 1 || vb <= 2 * nvec))
