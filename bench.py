@@ -542,6 +542,13 @@ def our_arm(args):
                                     "gbs": p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9}
             del x16
         ctx.free_gauge(gid)
+        # APE smearing of the links (FP64, staples + projection onto SU(3)), one step
+        gid = ctx.load_gauge(U, 4, dims, stream=stream)
+        ctx.ape_smear(gid, 0.5, 1, stream=stream)
+        p = ctx.get_profile()
+        ctx.free_gauge(gid)
+        extra["ape_smear"] = {"ms_per_step": p["ms_total"], "alpha": 0.5,
+                              "site_links_per_s": 3 * V / (p["ms_total"] / 1e3)}
         if rank == 0 and ws >= 1:
             # CPU baseline: the oracle on a bounded sample, on this machine's host cores
             Lx, Ly, Lz, Lt = dims

@@ -131,6 +131,24 @@ tls_status tls_build_twolink(tls_ctx *ctx, tls_gauge_id id, int wprec, int recon
  * Errors: TLS_ERR_NOT_FOUND, TLS_ERR_STATE (U released), TLS_ERR_UNSUPPORTED. */
 tls_status tls_build_links(tls_ctx *ctx, tls_gauge_id id, int prec, int keep_U, void *stream);
 
+/* ---- gauge-smeared links (Sec. 2, the remark after Eq. tlSmear) -------------
+ * Replaces the resident FP64 spatial links of gauge `id` by n_steps steps of
+ * APE smearing, each computed from the previous links (out of place):
+ *     V_mu(x) = (1 - alpha) U_mu(x) + (alpha/4) sum_{nu != mu, spatial} [
+ *         U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) ]
+ *     U'_mu(x) = P(V_mu(x)),
+ * P being the projection onto SU(3): the unitary polar factor (Newton's
+ * iteration X <- (X + X^-dag)/2) times exp(-i phi/3), phi = arg det in
+ * (-pi, pi].  Staples stay inside each time slice; periodic in x, y, z.  The
+ * two-link field and the one-link field built before become invalid
+ * (tls_smear then returns TLS_ERR_NOT_BUILT until tls_build_twolink runs
+ * again).  Allocates one temporary copy of the links.
+ * Errors: TLS_ERR_NOT_FOUND, TLS_ERR_STATE (U released), TLS_ERR_ARG
+ * (n_steps < 0 or alpha outside [0, 1]), TLS_ERR_DEVICE (a projection met a
+ * singular matrix or did not settle; that link kept its previous value),
+ * memory and CUDA errors.                                                     */
+tls_status tls_ape_smear(tls_ctx *ctx, tls_gauge_id id, double alpha, int n_steps, void *stream);
+
 /* Releases U, W and everything cached for gauge `id`. */
 tls_status tls_free_gauge(tls_ctx *ctx, tls_gauge_id id);
 

@@ -15,6 +15,9 @@ Functions (all FP64, complex numbers as numpy complex128):
 - ``smear_unfused(U, psi, n, sigma, t0)``
 - ``apply_hop(U, psi, t0)``         one-link hopping H psi          (Eq. 2)
 - ``smear_onelink(U, psi, n, alpha, t0)``  (1 + alpha H)^n psi     (Eq. 3, C = 1)
+- ``su3_project(M)``                projection of 3x3 matrices onto SU(3)
+- ``ape_smear(U, alpha, n)``        APE-smeared spatial links (Sec. 2, the remark
+                                    on gauge-smeared links after Eq. tlSmear)
 
 Array shapes: ``U`` is ``[Lt, Lz, Ly, Lx, nd, 3, 3]`` (nd = 3 or 4, mu order
 x, y, z[, t]); ``W`` is ``[Lt, Lz, Ly, Lx, 3, 3, 3]``; ``psi`` is
@@ -74,6 +77,10 @@ def _load():
         lib.oracle_apply_hop.restype = None
         lib.oracle_smear_onelink.argtypes = [P, I, P, P, I, I, D, I]
         lib.oracle_smear_onelink.restype = I
+        lib.oracle_su3_project.argtypes = [P, P]
+        lib.oracle_su3_project.restype = I
+        lib.oracle_ape.argtypes = [P, I, P, D, I, P]
+        lib.oracle_ape.restype = I
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = I
         _lib = lib
@@ -189,3 +196,34 @@ def smear_onelink(U, psi, n: int, alpha: float, t0: int = -1) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle_smear_onelink failed (%d)" % rc)
     return out[0] if single else out
+
+
+def su3_project(M) -> np.ndarray:
+    """Nearest SU(3) matrix of each 3x3 complex matrix in M (shape [..., 3, 3]):
+    the unitary polar factor by Newton's iteration, then the determinant phase
+    removed by its principal cube root."""
+    M = _c128(M)
+    assert M.shape[-2:] == (3, 3)
+    flat = np.ascontiguousarray(M.reshape(-1, 3, 3))
+    out = np.empty_like(flat)
+    lib = _load()
+    for k in range(flat.shape[0]):
+        src = np.ascontiguousarray(flat[k])
+        dst = np.empty_like(src)
+        if lib.oracle_su3_project(_ptr(src), _ptr(dst)) != 0:
+            raise ValueError("oracle_su3_project: singular or not converged")
+        out[k] = dst
+    return out.reshape(M.shape)
+
+
+def ape_smear(U, alpha: float, n: int) -> np.ndarray:
+    """n APE steps on the spatial links (staples in the three spatial
+    directions, weight alpha, projection onto SU(3)); returns [Lt, Lz, Ly, Lx, 3, 3, 3]."""
+    U = _c128(U)
+    assert U.ndim == 7 and U.shape[5:] == (3, 3) and U.shape[4] in (3, 4)
+    dims = _dims(U.shape)
+    out = np.zeros(U.shape[:4] + (3, 3, 3), dtype=np.complex128)
+    rc = _load().oracle_ape(_ptr(U), U.shape[4], _ptr(dims), float(alpha), int(n), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_ape: a projection failed")
+    return out

@@ -20,6 +20,8 @@
  *   - one-link hopping H psi(x) = sum_mu [ U_mu(x) psi(x + mu)
  *                                   + U_mu^dag(x - mu) psi(x - mu) ]  (Sec. 2, Eq. 2)
  *     and Gaussian smearing psi~ = C (1 + alpha H)^n psi with C = 1 (Sec. 2, Eq. 3)
+ *   - gauge-smeared links in place of U_mu (Sec. 2, the remark after
+ *     Eq. tlSmear): APE smearing with spatial staples and projection onto SU(3)
  *
  * Conventions (the paper is silent on them; these are the readings used):
  *   - "Delta" below is 4 Lap_two, so one smearing step is
@@ -41,6 +43,7 @@
  * decoupling, SU(3) closure of W, staggered-phase invariance of W, dense
  * brute force on tiny lattices.
  */
+#include <math.h>
 #include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
@@ -339,6 +342,152 @@ int oracle_smear_onelink(const double *U, int nd, const int L[4], double *psi, i
     }
     free(d);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauge-smeared links (Sec. 2: a smeared link may replace U_mu in the       */
+/* smearing operator).  APE smearing on each time slice with the spatial     */
+/* staples, every link updated from the previous iterate (Jacobi):           */
+/*   V_mu(x) = (1 - a) U_mu(x) + (a/4) sum_{nu != mu} [                       */
+/*       U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag                                    */
+/*     + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) ]                            */
+/*   U'_mu(x) = P(V_mu(x)): the unitary polar factor of V, times the cube     */
+/*   root of its inverse determinant phase (principal branch), so det = 1.    */
+/* ------------------------------------------------------------------------ */
+
+static void dagger(const double *a, double *d)
+{
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            d[(r * 3 + c) * 2] = a[(c * 3 + r) * 2];
+            d[(r * 3 + c) * 2 + 1] = -a[(c * 3 + r) * 2 + 1];
+        }
+}
+
+static cplx det3(const double *m)
+{
+    /* cofactor expansion along row 0 */
+    cplx a = get(m, 0), b = get(m, 1), c = get(m, 2);
+    cplx d = get(m, 3), e = get(m, 4), f = get(m, 5);
+    cplx g = get(m, 6), h = get(m, 7), i = get(m, 8);
+    cplx ei = cmul(e, i), fh = cmul(f, h), di = cmul(d, i), fg = cmul(f, g), dh = cmul(d, h), eg = cmul(e, g);
+    cplx t0 = cmul(a, (cplx){ei.re - fh.re, ei.im - fh.im});
+    cplx t1 = cmul(b, (cplx){di.re - fg.re, di.im - fg.im});
+    cplx t2 = cmul(c, (cplx){dh.re - eg.re, dh.im - eg.im});
+    cplx r = {t0.re - t1.re + t2.re, t0.im - t1.im + t2.im};
+    return r;
+}
+
+/* inv = m^-1 by the adjugate; returns -1 if det(m) is zero. */
+static int inverse3(const double *m, double *inv)
+{
+    cplx det = det3(m);
+    double n2 = det.re * det.re + det.im * det.im;
+    if (!(n2 > 0.0)) return -1;
+    cplx rdet = {det.re / n2, -det.im / n2};
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            /* cofactor of element (c, r): rows != c, columns != r */
+            int r0 = c == 0 ? 1 : 0, r1 = c == 2 ? 1 : 2;
+            int c0 = r == 0 ? 1 : 0, c1 = r == 2 ? 1 : 2;
+            cplx p = cmul(get(m, r0 * 3 + c0), get(m, r1 * 3 + c1));
+            cplx q = cmul(get(m, r0 * 3 + c1), get(m, r1 * 3 + c0));
+            cplx cof = {p.re - q.re, p.im - q.im};
+            if ((r + c) & 1) { cof.re = -cof.re; cof.im = -cof.im; }
+            cplx v = cmul(cof, rdet);
+            inv[(r * 3 + c) * 2] = v.re;
+            inv[(r * 3 + c) * 2 + 1] = v.im;
+        }
+    return 0;
+}
+
+/* Projection onto SU(3) of a nonsingular 3x3 complex matrix M: Newton's
+ * iteration X <- (X + X^-dag) / 2 for the unitary polar factor, stopped one
+ * step after the change falls below 1e-12 (the iteration converges
+ * quadratically), then X exp(-i phi/3) with phi = arg det X in (-pi, pi].
+ * Returns 0, or -1 for a singular matrix or no convergence in 100 steps. */
+int oracle_su3_project(const double *M, double *out)
+{
+    double X[18], Xi[18], Xid[18];
+    memcpy(X, M, sizeof X);
+    int settled = 0;
+    for (int it = 0; it < 100; ++it) {
+        if (inverse3(X, Xi) != 0) return -1;
+        dagger(Xi, Xid);
+        double d2 = 0.0;
+        for (int k = 0; k < 18; ++k) {
+            double nx = 0.5 * (X[k] + Xid[k]);
+            d2 += (nx - X[k]) * (nx - X[k]);
+            X[k] = nx;
+        }
+        if (settled) {
+            settled = 2;
+            break;
+        }
+        if (sqrt(d2) < 1e-12) settled = 1;
+    }
+    if (settled != 2) return -1;
+    cplx det = det3(X);
+    double phi = atan2(det.im, det.re);
+    cplx ph = {cos(phi / 3.0), -sin(phi / 3.0)};
+    for (int k = 0; k < 9; ++k) {
+        cplx v = cmul(get(X, k), ph);
+        out[2 * k] = v.re;
+        out[2 * k + 1] = v.im;
+    }
+    return 0;
+}
+
+/* n APE steps with weight a on every spatial link; out has nd = 3 layout
+ * [t][z][y][x][mu][3][3][2].  Returns 0, or -1 if a projection failed. */
+int oracle_ape(const double *U, int nd, const int L[4], double a, int n, double *out)
+{
+    const long V = (long)L[0] * L[1] * L[2] * L[3];
+    double *cur = (double *)malloc(sizeof(double) * V * 3 * 18);
+    if (!cur) return -1;
+    for (long s = 0; s < V; ++s)
+        for (int mu = 0; mu < 3; ++mu) memcpy(cur + (s * 3 + mu) * 18, link_at(U, nd, s, mu), sizeof(double) * 18);
+    int status = 0;
+    for (int step = 0; step < n && status == 0; ++step) {
+#pragma omp parallel for collapse(2) schedule(static) reduction(min : status)
+        for (int t = 0; t < L[3]; ++t)
+            for (int z = 0; z < L[2]; ++z)
+                for (int y = 0; y < L[1]; ++y)
+                    for (int x = 0; x < L[0]; ++x) {
+                        const long s = site_of(L, x, y, z, t);
+                        for (int mu = 0; mu < 3; ++mu) {
+                            double Vm[18], st[18], tmp[18], tmp2[18], dg[18];
+                            for (int k = 0; k < 18; ++k) st[k] = 0.0;
+                            for (int nu = 0; nu < 3; ++nu) {
+                                if (nu == mu) continue;
+                                const long xp_nu = neighbour(L, x, y, z, t, nu, 1);
+                                const long xp_mu = neighbour(L, x, y, z, t, mu, 1);
+                                const long xm_nu = neighbour(L, x, y, z, t, nu, -1);
+                                int c[3] = {x, y, z};
+                                c[nu] = wrap(c[nu] - 1, L[nu]);
+                                c[mu] = wrap(c[mu] + 1, L[mu]);
+                                const long xm_nu_p_mu = site_of(L, c[0], c[1], c[2], t);
+                                /* forward staple */
+                                matmul(cur + (s * 3 + nu) * 18, cur + (xp_nu * 3 + mu) * 18, tmp);
+                                dagger(cur + (xp_mu * 3 + nu) * 18, dg);
+                                matmul(tmp, dg, tmp2);
+                                for (int k = 0; k < 18; ++k) st[k] += tmp2[k];
+                                /* backward staple */
+                                dagger(cur + (xm_nu * 3 + nu) * 18, dg);
+                                matmul(dg, cur + (xm_nu * 3 + mu) * 18, tmp);
+                                matmul(tmp, cur + (xm_nu_p_mu * 3 + nu) * 18, tmp2);
+                                for (int k = 0; k < 18; ++k) st[k] += tmp2[k];
+                            }
+                            const double *u = cur + (s * 3 + mu) * 18;
+                            for (int k = 0; k < 18; ++k) Vm[k] = (1.0 - a) * u[k] + 0.25 * a * st[k];
+                            if (oracle_su3_project(Vm, out + (s * 3 + mu) * 18) != 0) status = -1;
+                        }
+                    }
+        memcpy(cur, out, sizeof(double) * V * 3 * 18);
+    }
+    if (n == 0) memcpy(out, cur, sizeof(double) * V * 3 * 18);
+    free(cur);
+    return status;
 }
 
 /* Number of OpenMP threads a parallel region here uses (1 without OpenMP). */

@@ -432,6 +432,61 @@ tls_status tls_build_twolink(tls_ctx *ctx, tls_gauge_id id, int wprec, int recon
     return ok();
 }
 
+tls_status tls_ape_smear(tls_ctx *ctx, tls_gauge_id id, double alpha, int n_steps, void *stream)
+{
+    if (!ctx) return fail(TLS_ERR_ARG, "tls_ape_smear: ctx is NULL");
+    std::lock_guard<FairMutex> lk(ctx->mu);
+    Gauge *gg = find_gauge(ctx, id);
+    if (!gg) return fail(TLS_ERR_NOT_FOUND, "tls_ape_smear: unknown gauge id %lld", (long long)id);
+    if (!gg->Up) return fail(TLS_ERR_STATE, "tls_ape_smear: the links of gauge %lld were released", (long long)id);
+    if (n_steps < 0 || !(alpha >= 0.0 && alpha <= 1.0))
+        return fail(TLS_ERR_ARG, "tls_ape_smear: n_steps %d, alpha %g", n_steps, alpha);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the derived fields no longer match the links
+    gg->built = false;
+    if (gg->L1) {
+        dev_free(ctx, gg->L1, gg->L1_bytes);
+        gg->L1 = nullptr;
+        gg->L1_bytes = 0;
+        gg->l1fmt = -1;
+    }
+    if (n_steps == 0) return ok();
+    double *tmp = nullptr;
+    tls_status s = dev_alloc(ctx, (void **)&tmp, gg->Up_bytes, "tls_ape_smear: link copy");
+    if (s != TLS_OK) return s;
+    cudaError_t e = cudaMemsetAsync(tmp, 0, gg->Up_bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st);
+    if (ctx->profiling) cudaEventRecord(ctx->ev[0], st);
+    double *cur = gg->Up, *nxt = tmp;
+    const int nblk = gg->L[3] * 8;
+    for (int k = 0; k < n_steps && e == cudaSuccess; ++k) {
+        e = launch_ape_step(cur, nxt, gg->g, nblk, alpha, ctx->d_err, st);
+        std::swap(cur, nxt);
+    }
+    if (ctx->profiling) cudaEventRecord(ctx->ev[1], st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dev_free(ctx, tmp, gg->Up_bytes);
+        return cuda_fail(e, "tls_ape_smear");
+    }
+    // keep the buffer that holds the result, free the other
+    gg->Up = cur;
+    dev_free(ctx, nxt, gg->Up_bytes);
+    if (ctx->profiling) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+        ctx->prof = tls_profile{};
+        ctx->prof.ms_total = ms;
+        ctx->prof.launches = n_steps;
+    }
+    if (herr & DERR_PROJECT)
+        return fail(TLS_ERR_DEVICE, "tls_ape_smear: a link projection met a singular matrix or did not settle");
+    return ok();
+}
+
 tls_status tls_build_links(tls_ctx *ctx, tls_gauge_id id, int prec, int keep_U, void *stream)
 {
     if (!ctx) return fail(TLS_ERR_ARG, "tls_build_links: ctx is NULL");

@@ -105,6 +105,9 @@ cudaError_t launch_build_twolink(const double *Up, char *W, int wfmt, const SubG
                                  cudaStream_t s);
 // The one-link field: U itself rounded into a W format (same planes as W).
 cudaError_t launch_build_links(const double *Up, char *L1, int wfmt, const SubGeom &g, int nblk, cudaStream_t s);
+// One APE step on the packed spatial links: out = P((1-a) U + (a/4) staples) (k_ape.cu).
+cudaError_t launch_ape_step(const double *U, double *out, const SubGeom &g, int nblk, double a, int *err,
+                            cudaStream_t s);
 cudaError_t launch_export_twolink(const char *W, int wfmt, double *out, const SubGeom &g, const int L[4],
                                   cudaStream_t s);
 // Whether the interleaved pack/unpack use the row transposes (contiguous canonical rows).

@@ -50,6 +50,7 @@ enum DevErr {
     DERR_BOUNDS = 1,      // an index check failed (checked builds)
     DERR_TIMEOUT = 2,     // a bounded barrier ran out of polls
     DERR_RECON8 = 4,      // 8-real form met |W00| ~ 1
+    DERR_PROJECT = 8,     // a link projection onto SU(3) met a singular matrix or did not settle
 };
 
 }  // namespace tls

@@ -47,7 +47,7 @@ EXPORTS = (
     "tls_create", "tls_destroy", "tls_last_error", "tls_version", "tls_bytes_in_use",
     "tls_load_gauge", "tls_build_twolink", "tls_free_gauge", "tls_export_twolink",
     "tls_export_gauge", "tls_smear", "tls_set_profiling", "tls_get_profile",
-    "tls_smear_noalloc", "tls_build_links", "tls_smear_onelink", "tls_set_barrier_budget", "tls_autotune", "tls_tune_set", "tls_serve_start", "tls_serve_stop", "tls_serve_submit",
+    "tls_smear_noalloc", "tls_build_links", "tls_ape_smear", "tls_smear_onelink", "tls_set_barrier_budget", "tls_autotune", "tls_tune_set", "tls_serve_start", "tls_serve_stop", "tls_serve_submit",
     "tls_serve_poll", "tls_serve_wait",
 )
 
@@ -105,6 +105,7 @@ def _load() -> ctypes.CDLL:
         "tls_smear": ([P, I64, P, I, I, I, I, D, I, I, I, P, P], I),
         "tls_smear_noalloc": ([P, I64, P, I, I, I, D, I, I, P], I),
         "tls_build_links": ([P, I64, I, I, P], I),
+        "tls_ape_smear": ([P, I64, D, I, P], I),
         "tls_smear_onelink": ([P, I64, P, I, I, I, I, D, I, I, P, P], I),
         "tls_set_profiling": ([P, I], I),
         "tls_get_profile": ([P, ctypes.POINTER(tls_profile)], I),
@@ -225,6 +226,11 @@ def tls_smear(ctx, gauge: int, vecs, io_prec: int, nvec: int, N: int, width: flo
 
 def tls_build_links(ctx, gauge: int, prec: int = TLS_F32, keep_U: int = 1, stream=None) -> None:
     _check(lib.tls_build_links(ctx, int(gauge), int(prec), int(keep_U), _stream(stream)))
+
+
+def tls_ape_smear(ctx, gauge: int, alpha: float, n_steps: int, stream=None) -> None:
+    """Replaces the resident links by n_steps APE steps (projection onto SU(3))."""
+    _check(lib.tls_ape_smear(ctx, int(gauge), float(alpha), int(n_steps), _stream(stream)))
 
 
 def tls_smear_onelink(ctx, gauge: int, vecs, io_prec: int, nvec: int, N: int, alpha: float,
@@ -358,6 +364,9 @@ class Context:
 
     def build_links(self, gauge, prec=TLS_F32, keep_U=1, stream=None):
         return tls_build_links(self.h, gauge, prec, keep_U, stream)
+
+    def ape_smear(self, gauge, alpha, n_steps, stream=None):
+        return tls_ape_smear(self.h, gauge, alpha, n_steps, stream)
 
     def smear_onelink(self, gauge, vecs, io_prec, nvec, N, alpha, timeslice=TLS_ALL_T, storage=TLS_F32,
                       stream=None, norms=False):

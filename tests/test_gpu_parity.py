@@ -523,3 +523,68 @@ def test_sink_smear_workload_sampled(ctx, T):
         assert rel_l2(got, want) <= tol(T.TLS_F32, w["N"])
     del vecs, U
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------------ APE-smeared links (Sec. 2)
+@pytest.mark.parametrize("dims,alpha,n", [((6, 4, 8, 2), 0.45, 3), ((4, 4, 4, 1), 0.7, 1), ((8, 6, 4, 3), 0.2, 2)])
+def test_ape_matches_oracle(ctx, T, dims, alpha, n):
+    U = gauge(dims, "haar", 61)
+    want = oracle.ape_smear(U.numpy(), alpha, n)
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.ape_smear(gid, alpha, n)
+    got = np.zeros_like(want)
+    ctx.export_gauge(gid, got)
+    ctx.free_gauge(gid)
+    assert np.abs(got - want).max() < 1e-12
+
+
+def test_ape_then_twolink_smear(ctx, T):
+    """Smeared links feed the two-link build: the whole chain against the oracle's."""
+    dims = (6, 6, 4, 2)
+    U = gauge(dims, "near", 62, eps=0.4)
+    vecs = synth.gaussian_vectors(dims, 3, 63)
+    Ua = oracle.ape_smear(U.numpy(), 0.5, 2)
+    want = oracle.smear(oracle.twolink(Ua), vecs.numpy(), 7, 1.4)
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.ape_smear(gid, 0.5, 2)
+    ctx.build_twolink(gid, T.TLS_F64, 18)
+    x = vecs.clone().cuda()
+    ctx.smear(gid, x, T.TLS_F64, 3, 7, 1.4, storage=T.TLS_F64, kernel=T.TLS_KERNEL_MRHS)
+    ctx.free_gauge(gid)
+    assert max(per_vector_rel_l2(x.cpu().numpy(), want)) <= 1e-13
+
+
+def test_ape_pure_gauge_and_state(ctx, T):
+    dims = (4, 6, 4, 2)
+    G = synth.gauge_transform_haar(dims, 64).numpy()
+    U = np.empty(G.shape[:4] + (3, 3, 3), dtype=np.complex128)
+    for i, ax in enumerate((3, 2, 1)):
+        U[..., i, :, :] = G @ np.conj(np.swapaxes(np.roll(G, -1, axis=ax), -1, -2))
+    gid = ctx.load_gauge(torch.from_numpy(U), 3, dims)
+    ctx.build_twolink(gid, T.TLS_F32, 18)
+    ctx.ape_smear(gid, 0.6, 2)
+    got = np.zeros_like(U)
+    ctx.export_gauge(gid, got)
+    assert np.abs(got - U).max() < 1e-12
+    x = synth.gaussian_vectors(dims, 1, 65, dtype=torch.complex64).cuda()
+    with pytest.raises(T.TLSError) as e:  # W predates the smearing
+        ctx.smear(gid, x, T.TLS_F32, 1, 2, 0.5)
+    assert e.value.status == T.TLS_ERR_NOT_BUILT
+    with pytest.raises(T.TLSError) as e:
+        ctx.ape_smear(gid, 1.5, 1)
+    assert e.value.status == T.TLS_ERR_ARG
+    ctx.free_gauge(gid)
+
+
+def test_ape_large_lattice_sampled(ctx, T):
+    """32^3 x 4: one slice of the device result against the oracle on that slice alone."""
+    dims = (32, 32, 32, 4)
+    U = gauge_dev(dims, "near", 66, eps=0.3, nd=4)
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.ape_smear(gid, 0.5, 2)
+    got = torch.zeros(dims[3], dims[2], dims[1], dims[0], 3, 3, 3, dtype=torch.complex128, device="cuda")
+    ctx.export_gauge(gid, got)
+    ctx.free_gauge(gid)
+    t = 2
+    want = oracle.ape_smear(U[t:t + 1].cpu().numpy(), 0.5, 2)
+    assert np.abs(got[t:t + 1].cpu().numpy() - want).max() < 1e-12

@@ -413,3 +413,90 @@ def test_twolink_is_the_straight_part_of_h_squared():
     # and the full one-link H is the sum of the six single hops
     h = sum(hop_dir(psi, mu, s) for mu in range(3) for s in (1, -1))
     assert rel_l2(oracle.apply_hop(U, psi), h) < 1e-14
+
+
+# --------------------------------------------------------------------------- APE
+# Gauge-smeared links (Sec. 2, the remark after Eq. tlSmear): APE smearing with
+# the spatial staples and projection onto SU(3).
+def _svd_su3(M):
+    """Independent projection: unitary polar factor from numpy's SVD, det phase removed."""
+    u, _, vh = np.linalg.svd(M)
+    W = u @ vh
+    ph = np.exp(-1j * np.angle(np.linalg.det(W)) / 3)
+    return W * ph[..., None, None]
+
+
+def test_ape_projection_is_the_polar_factor():
+    rng = np.random.default_rng(51)
+    M = rng.normal(size=(40, 3, 3)) + 1j * rng.normal(size=(40, 3, 3))
+    P = oracle.su3_project(M)
+    assert np.abs(P - _svd_su3(M)).max() < 1e-12
+    # a positive multiple of an SU(3) matrix projects back onto it
+    S = _gauge((2, 2, 2, 1), 52, "haar", nd=3)[0, 0, 0, 0]
+    assert np.abs(oracle.su3_project(2.5 * S) - S).max() < 1e-13
+
+
+def test_ape_identity_cases():
+    dims = (4, 4, 4, 2)
+    U = _gauge(dims, 53, "haar", nd=4)
+    assert np.abs(oracle.ape_smear(U, 0.0, 3) - U[..., :3, :, :]).max() < 1e-13
+    assert np.array_equal(oracle.ape_smear(U, 0.7, 0), U[..., :3, :, :])
+    one = synth.gauge_unit(dims, nd=3).numpy()
+    assert np.abs(oracle.ape_smear(one, 0.6, 4) - one).max() < 1e-14
+
+
+def test_ape_pure_gauge_is_invariant():
+    """U_mu(x) = G(x) G(x+mu)^dag has unit plaquettes: every staple equals the link."""
+    dims = (4, 6, 4, 2)
+    G = synth.gauge_transform_haar(dims, 54).numpy()
+    U = np.empty(G.shape[:4] + (3, 3, 3), dtype=np.complex128)
+    for i, ax in enumerate((3, 2, 1)):
+        U[..., i, :, :] = G @ np.conj(np.swapaxes(_shift(G, ax, 1), -1, -2))
+    assert np.abs(oracle.ape_smear(U, 0.6, 3) - U).max() < 1e-12
+
+
+def test_ape_gauge_covariance():
+    dims = (4, 4, 6, 2)
+    U = _gauge(dims, 55, "haar", nd=3)
+    G = synth.gauge_transform_haar(dims, 56).numpy()
+
+    def transform(A):
+        out = np.empty_like(A)
+        for i, ax in enumerate((3, 2, 1)):
+            out[..., i, :, :] = G @ A[..., i, :, :] @ np.conj(np.swapaxes(_shift(G, ax, 1), -1, -2))
+        return out
+
+    a = oracle.ape_smear(transform(U), 0.45, 2)
+    b = transform(oracle.ape_smear(U, 0.45, 2))
+    assert np.abs(a - b).max() < 1e-12
+
+
+def test_ape_single_excited_link():
+    """All links 1 except U_x at the origin = R: the staples that contain R are
+    known by hand, and their projections are taken with numpy's SVD."""
+    dims = (4, 4, 4, 1)
+    U = synth.gauge_unit(dims, nd=3).numpy().copy()
+    R = _gauge((2, 2, 2, 1), 57, "haar", nd=3)[0, 0, 0, 0, 0]
+    U[0, 0, 0, 0, 0] = R  # [t, z, y, x, mu]
+    a = 0.4
+    out = oracle.ape_smear(U, a, 1)
+    I = np.eye(3)
+    expect = {
+        # link (x, y, z, mu): V before projection
+        (0, 0, 0, 0): (1 - a) * R + a * I,                      # its own staples are all 1
+        (0, 0, 0, 1): (1 - a) * I + a / 4 * (R + 3 * I),        # forward nu = x staple: R 1 1^dag
+        (1, 0, 0, 1): (1 - a) * I + a / 4 * (R.conj().T + 3 * I),  # backward nu = x staple: R^dag 1 1
+        (0, 1, 0, 0): (1 - a) * I + a / 4 * (R + 3 * I),        # backward nu = y staple: 1^dag R 1
+        (0, 3, 0, 0): (1 - a) * I + a / 4 * (R + 3 * I),        # forward nu = y staple: 1 R 1^dag
+        (0, 0, 1, 0): (1 - a) * I + a / 4 * (R + 3 * I),        # backward nu = z staple
+        (2, 2, 2, 0): I,                                        # far from the origin
+    }
+    for (x, y, z, mu), V in expect.items():
+        assert np.abs(out[0, z, y, x, mu] - _svd_su3(V)).max() < 1e-13, (x, y, z, mu)
+
+
+def test_ape_output_is_su3():
+    U = _gauge((4, 4, 4, 2), 58, "haar", nd=4)
+    A = oracle.ape_smear(U, 0.5, 3)
+    assert np.abs(A @ np.conj(np.swapaxes(A, -1, -2)) - np.eye(3)).max() < 1e-13
+    assert np.abs(np.linalg.det(A) - 1).max() < 1e-13
