@@ -381,6 +381,31 @@ def sink_run(T, ctx, device, stream, hbm_peak):
             "ms_per_step": p["ms_iter"] / N, "gbs": gbs, "frac": gbs / hbm_peak, "kernel": best}
 
 
+def small_lattice_run(T, ctx, device, stream, hbm_peak):
+    """16^3x32 (8^3 sublattice blocks), 24 corner walls, N = 80: the on-chip
+    persistent form (each block's W and iterates in one CTA's shared memory)
+    against the step-by-step kernels, all through the autotuner."""
+    import torch
+    from paper_2301_05518_gb300 import synth
+    dims, nvec, N, sigma = (16, 16, 16, 32), 24, 80, 16.0
+    U = synth.gauge_near_unit(dims, 0.2, 1006, nd=4, device=device)
+    x = synth.corner_wall_sources(dims, t=0, dtype=torch.complex64, device=device)
+    gid = ctx.load_gauge(U, 4, dims, stream=stream)
+    ctx.build_twolink(gid, T.TLS_F32, T.TLS_R18, keep_U=0, stream=stream)
+    best, cands = ctx.autotune(gid, nvec, T.TLS_F32, T.TLS_ALL_T, steps=N)
+    ctx.smear(gid, x, T.TLS_F32, nvec, N, sigma, storage=T.TLS_F32, stream=stream)
+    p = ctx.get_profile()
+    ctx.free_gauge(gid)
+    onchip = [c for c in cands if c["kernel"] == T.TLS_KERNEL_PERSISTENT and tuple(c["tile"]) == (0, 1, 0)]
+    steps = [c for c in cands if c["kernel"] != T.TLS_KERNEL_PERSISTENT]
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    return {"workload": "16^3x32 24 corner-wall sources N=80", "best": best,
+            "ms_per_step": p["ms_iter"] / N, "vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3),
+            "onchip_ms_per_step": min((c["ms_per_step"] for c in onchip), default=None),
+            "best_step_kernel_ms_per_step": min((c["ms_per_step"] for c in steps), default=None),
+            "effective_gbs": V * (216 + 48 * nvec) / (p["ms_iter"] / N / 1e3) / 1e9}
+
+
 def our_arm(args):
     import torch
     ws, rank, local = dist_setup("nccl")
@@ -563,6 +588,8 @@ def our_arm(args):
         del U, vecs
         torch.cuda.empty_cache()
         extra["sink_smear"] = sink_run(T, ctx, local, stream, hbm_peak)
+        torch.cuda.empty_cache()
+        extra["small_lattice"] = small_lattice_run(T, ctx, local, stream, hbm_peak)
         torch.cuda.empty_cache()
         extra["serving"] = serving_run(T, local, n_closed=24, n_open=args.serve_jobs, time_cap_s=25.0,
                                        fp64_cap_s=10.0)

@@ -267,7 +267,10 @@ typedef struct {
     int tile[3];            /* multi-RHS kernel: tile[0] > 0 sets the sites    */
                             /* per CTA (a strip along x'); persistent kernel:  */
                             /* tile[0] > 0 sets the L2 budget of one group of  */
-                            /* blocks in MB (default 48); multi-RHS kernel:    */
+                            /* blocks in MB (default 48), tile[1] = 1 selects  */
+                            /* the on-chip form (one CTA per block keeps W and */
+                            /* the iterates in shared memory, when they fit);  */
+                            /* multi-RHS kernel:                               */
                             /* tile[1] = 1 stages the strip's W in shared      */
                             /* memory, tile[1] = 2 as well and applies it with */
                             /* packed FP32 pair FMAs (not FP64), tile[1] = 3   */

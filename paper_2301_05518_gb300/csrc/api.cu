@@ -733,7 +733,14 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
 
     // Persistent-kernel plan: co-resident grid, L2-sized groups, scratch.
     PersistArgs pa{};
-    if (kern == TLS_KERNEL_PERSISTENT && N > 0) {
+    // tile[1] = 1: the on-chip form, when a block's W and scratch fit in shared memory
+    if (kern == TLS_KERNEL_PERSISTENT && N > 0 && tile[1] == 1 &&
+        onchip_plan(g, wfmt_bytes(fmt), vfmt_bytes(storage == TLS_F64 ? P_F64 : P_F32), nvec,
+                    ctx->max_smem, &pa.nvg, &pa.smem)) {
+        pa.onchip = 1;
+        pa.sprec = storage == TLS_F64 ? P_F64 : P_F32;
+    } else if (kern == TLS_KERNEL_PERSISTENT && N > 0) {
+        threads = std::min(threads, 256);  // the grid-wide form is built for CTAs of <= 256 threads
         const int sprec = storage == TLS_F64 ? P_F64 : P_F32;
         const int occ = persistent_occupancy(fmt, storage, sprec, vb, threads);
         if (occ <= 0) return fail(TLS_ERR_UNSUPPORTED, "tls_smear: persistent kernel cannot be resident");

@@ -839,8 +839,95 @@ template <int VP, int WF, int VB> cudaError_t step_launch(const StepArgs &a)
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------------------------
+// On-chip persistent form: the (slice, sublattice) blocks never couple, so
+// one CTA per (block, vector group) runs all N steps inside its own shared
+// memory: W of the block and two scratch copies of the group's iterates
+// (plane stride Pss = Vs rounded up to 4), with __syncthreads between steps
+// and no inter-CTA wait.  The iterates stay in the scratch precision (FP32,
+// FP64 for FP64 storage) and are converted to the storage precision only on
+// the way in and out, which is what k_persist computes: the results are
+// bitwise equal.
+// --------------------------------------------------------------------------
+template <int VP, int WF, int VB>
+__global__ void __launch_bounds__(1024) k_persist_blk(const char *__restrict__ W, const char *__restrict__ in,
+                                                     char *__restrict__ out, const double *__restrict__ alpha,
+                                                     SubGeom g, int nvec, int N, int nvg, int64_t vs)
+{
+    constexpr int SP = scratch_prec<VP>();
+    constexpr int WB = wfmt_bytes(WF);
+    constexpr int VBY = vfmt_bytes(VP), SBY = vfmt_bytes(SP);
+    constexpr int NQ = WB / 16, REM = WB % 16;
+    typedef typename VFmt<SP>::R R;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int b = blockIdx.x;
+    const int v0 = blockIdx.y * nvg;
+    const int nv = min(nvg, nvec - v0);
+    const int Pss = (g.Vs + 3) / 4 * 4;
+    SubGeom gs = g;
+    gs.Ps = Pss;
+    char *Ws = reinterpret_cast<char *>(sm);
+    char *S0 = Ws + (int64_t)3 * Pss * WB;
+    char *S1 = S0 + (int64_t)nvg * Pss * SBY;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    // W of block b, plane by plane (16-byte words, then the remainder plane)
+    for (int d = 0; d < 3; ++d) {
+        const char *src = W + ((int64_t)b * 3 + d) * g.Ps * WB;
+        char *dst = Ws + (int64_t)d * Pss * WB;
+        for (int e = tid; e < NQ * g.Vs; e += nth) {
+            const int j = e / g.Vs, i = e - j * g.Vs;
+            reinterpret_cast<uint4 *>(dst)[(int64_t)j * Pss + i] = reinterpret_cast<const uint4 *>(src)[(int64_t)j * g.Ps + i];
+        }
+        if constexpr (REM == 8) {
+            for (int i = tid; i < g.Vs; i += nth)
+                reinterpret_cast<uint2 *>(dst + (int64_t)NQ * Pss * 16)[i] =
+                    reinterpret_cast<const uint2 *>(src + (int64_t)NQ * g.Ps * 16)[i];
+        } else if constexpr (REM == 4) {
+            for (int i = tid; i < g.Vs; i += nth)
+                reinterpret_cast<uint32_t *>(dst + (int64_t)NQ * Pss * 16)[i] =
+                    reinterpret_cast<const uint32_t *>(src + (int64_t)NQ * g.Ps * 16)[i];
+        }
+    }
+    // the group's vectors, converted to the scratch precision
+    for (int e = tid; e < nv * g.Vs; e += nth) {
+        const int v = e / g.Vs, i = e - v * g.Vs;
+        cpx<R> p[3];
+        VFmt<VP>::template load<false>(in + (int64_t)(v0 + v) * vs + (int64_t)b * g.Ps * VBY, g.Ps, i, p);
+        VFmt<SP>::template store<false>(S0 + (int64_t)v * Pss * SBY, Pss, i, p);
+    }
+    __syncthreads();
+    const int nchunk = (nv + VB - 1) / VB;
+    const int64_t sst = (int64_t)Pss * SBY;
+    for (int it = 0; it < N; ++it) {
+        const char *src = (it & 1) ? S1 : S0;
+        char *dst = (it & 1) ? S0 : S1;
+        for (int w = tid; w < nchunk * g.Vs; w += nth) {
+            const int c = w / g.Vs, i = w - c * g.Vs;
+            site_step<SP, SP, WF, VB, false, false>(Ws, src, dst, alpha + v0, gs, 0, i, c * VB, nv, sst, sst, 0, 0);
+        }
+        __syncthreads();
+    }
+    const char *res = (N & 1) ? S1 : S0;
+    for (int e = tid; e < nv * g.Vs; e += nth) {
+        const int v = e / g.Vs, i = e - v * g.Vs;
+        cpx<R> p[3];
+        VFmt<SP>::template load<false>(res + (int64_t)v * Pss * SBY, Pss, i, p);
+        VFmt<VP>::template store<false>(out + (int64_t)(v0 + v) * vs + (int64_t)b * g.Ps * VBY, g.Ps, i, p);
+    }
+}
+
 template <int VP, int WF, int VB> cudaError_t persist_launch(const PersistArgs &a)
 {
+    if (a.onchip) {
+        cudaError_t e = cudaFuncSetAttribute(k_persist_blk<VP, WF, VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             a.smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid(a.nblk, (a.nvec + a.nvg - 1) / a.nvg);
+        if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+        k_persist_blk<VP, WF, VB><<<grid, a.threads, a.smem, a.stream>>>(a.W, a.in, a.out, a.alpha, a.g, a.nvec, a.N,
+                                                                           a.nvg, a.vstride);
+        return cudaGetLastError();
+    }
     void *args[] = {(void *)&a.W,  (void *)&a.in,   (void *)&a.out,    (void *)&a.scr[0], (void *)&a.scr[1],
                     (void *)&a.alpha, (void *)&a.g, (void *)&a.nblk, (void *)&a.nvec,   (void *)&a.N,
                     (void *)&a.group_blocks, (void *)&a.vstride, (void *)&a.sstride, (void *)&a.bar,

@@ -1,6 +1,8 @@
 // tls_internal.h -- host-side launch interface between the C ABI and the kernels.
 #pragma once
 
+#include <algorithm>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,8 +49,27 @@ struct PersistArgs {
     int *err;              // device error word
     long long budget;      // polls per barrier
     int grid;              // CTAs (co-resident)
+    int onchip;            // 1: one CTA per (block, vector group) keeps W and the iterates in shared memory
+    int nvg;               // on-chip form: vectors per CTA
+    int smem;              // on-chip form: dynamic shared memory bytes
     cudaStream_t stream;
 };
+
+// On-chip persistent form: whether one (slice, sublattice) block's W and two
+// scratch copies of nvg vectors fit in max_smem bytes; fills nvg (<= nvec)
+// and the shared-memory bytes.  Host-only arithmetic.
+inline bool onchip_plan(const SubGeom &g, int wfmt_bytes_, int scratch_bytes, int nvec, int max_smem, int *nvg,
+                        int *smem)
+{
+    const int64_t Pss = (g.Vs + 3) / 4 * 4;
+    const int64_t wbytes = 3 * Pss * wfmt_bytes_;
+    const int64_t per_vec = 2 * Pss * scratch_bytes;
+    if (wbytes + per_vec > max_smem) return false;
+    const int64_t n = std::min<int64_t>(nvec, (max_smem - wbytes) / per_vec);
+    *nvg = (int)n;
+    *smem = (int)(wbytes + n * per_vec);
+    return true;
+}
 
 // Returns cudaErrorNotSupported for combinations without a kernel.
 cudaError_t launch_step(const StepArgs &a);

@@ -20,7 +20,7 @@ struct Cand {
     int tile[3];
 };
 
-std::vector<Cand> candidates(int nvec, int storage, bool rows)
+std::vector<Cand> candidates(int nvec, int storage, bool rows, bool onchip)
 {
     std::vector<Cand> c;
     if (nvec <= 4) {
@@ -52,6 +52,10 @@ std::vector<Cand> candidates(int nvec, int storage, bool rows)
         if (vb <= vmax && (vb == 1 || vb <= 2 * nvec))
             for (int mb : {48, 96})  // L2 budget of one group of blocks (MB)
                 c.push_back({TLS_KERNEL_PERSISTENT, vb, 256, {mb, 0, 0}});
+    if (onchip)  // every block's W and iterates in one CTA's shared memory
+        for (int vb : {1, 4})
+            if (vb <= vmax)
+                for (int t : {512, 1024}) c.push_back({TLS_KERNEL_PERSISTENT, vb, t, {0, 1, 0}});
     return c;
 }
 
@@ -108,7 +112,10 @@ tls_status tls_autotune(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
     int n = 0;
     const int G = std::min(nvec, 256);
     const bool rows = storage != TLS_F64 && rows_applicable(gg.wfmt, storage, gg.g, G, 1, ctx->max_smem);
-    for (const Cand &c : candidates(nvec, storage, rows)) {
+    int nvg = 0, smem = 0;
+    const bool onchip = onchip_plan(gg.g, wfmt_bytes(gg.wfmt), storage == TLS_F64 ? 48 : 24, nvec, ctx->max_smem,
+                                    &nvg, &smem);
+    for (const Cand &c : candidates(nvec, storage, rows, onchip)) {
         if (c.kernel == TLS_KERNEL_MRHS_ROWS && !rows_applicable(gg.wfmt, storage, gg.g, G, c.vb, ctx->max_smem))
             continue;
         // one warm-up call, then the timed one

@@ -588,3 +588,31 @@ def test_ape_large_lattice_sampled(ctx, T):
     t = 2
     want = oracle.ape_smear(U[t:t + 1].cpu().numpy(), 0.5, 2)
     assert np.abs(got[t:t + 1].cpu().numpy() - want).max() < 1e-12
+
+
+# ------------------------------------------------------------------ on-chip persistent form
+@pytest.mark.parametrize("dims,nvec,storage,vb", [((8, 8, 8, 3), 5, "F32", 1), ((16, 16, 16, 2), 6, "F32", 4),
+                                                  ((16, 8, 8, 2), 7, "F16", 1), ((8, 8, 8, 2), 3, "F64", 1),
+                                                  ((16, 16, 16, 1), 9, "BF16", 4), ((4, 4, 4, 2), 2, "F32", 1)])
+def test_persistent_onchip_bitwise_equals_l2_form(ctx, T, dims, nvec, storage, vb):
+    """One CTA per block with W and the iterates in shared memory == the grid-wide persistent kernel."""
+    st = getattr(T, "TLS_" + storage)
+    io = T.TLS_F64 if st == T.TLS_F64 else T.TLS_F32
+    dt = torch.complex128 if io == T.TLS_F64 else torch.complex64
+    U = gauge(dims, "haar", 71)
+    vecs = synth.gaussian_vectors(dims, nvec, 72, dtype=dt)
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.build_twolink(gid, T.TLS_F64 if st == T.TLS_F64 else T.TLS_F32, 18)
+    b = vecs.clone().cuda()
+    ctx.smear(gid, b, io, nvec, 9, 1.7, storage=st, kernel=T.TLS_KERNEL_PERSISTENT)
+    ctx.tune_set(gid, nvec, st, T.TLS_ALL_T, T.TLS_KERNEL_PERSISTENT, vb, 1024 if nvec % 2 else 512, (0, 1, 0))
+    a = vecs.clone().cuda()
+    ctx.set_profiling(True)
+    ctx.smear(gid, a, io, nvec, 9, 1.7, storage=st, kernel=T.TLS_KERNEL_AUTO)
+    assert ctx.get_profile()["kernel"] == T.TLS_KERNEL_PERSISTENT
+    ctx.set_profiling(False)
+    ctx.free_gauge(gid)
+    assert torch.equal(a, b)
+    if storage == "F32":
+        want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), 9, 1.7)
+        assert max(per_vector_rel_l2(a.cpu().numpy().astype(np.complex128), want)) <= 2e-6 * 9
