@@ -469,10 +469,11 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
 // results are bitwise equal to every other kernel.  Arithmetic in FP32 (FP32
 // and 16-bit storage).
 // --------------------------------------------------------------------------
-template <int VP, int WF, int VB, bool PRE>
+template <int VP, int WF, int VB, bool PRE, bool ACT = false>
 __global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, const char *__restrict__ in,
                                                   char *__restrict__ out, const double *__restrict__ alpha,
-                                                  const float *__restrict__ alphaf, SubGeom g, int nvec)
+                                                  const float *__restrict__ alphaf, const int *__restrict__ active,
+                                                  SubGeom g, int nvec)
 {
     static_assert(VP != P_F64, "packed FP32 pairs only");
     constexpr int WB = wfmt_bytes(WF);
@@ -547,6 +548,16 @@ __global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, co
     }
     __syncthreads();
     if (!act) return;
+    // ACT (serving): vectors whose slot is inactive are not stored
+    bool on[VB];
+    bool any = false, all = true;
+#pragma unroll
+    for (int k = 0; k < VB; ++k) {
+        on[k] = !ACT || active[il_vec<VP, VB>(t, T, k)] != 0;
+        any = any || on[k];
+        all = all && on[k];
+    }
+    if (!any) return;
     float2 acc[VB][3];
 #pragma unroll
     for (int v = 0; v < VB; ++v)
@@ -604,7 +615,13 @@ __global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, co
             o[v][r].im = u.y;
         }
     }
-    RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, cs, t, T, o);
+    if (all) {
+        RecGroup<VP, VB>::store(rout + (unsigned)i * rstride, cs, t, T, o);
+    } else {
+#pragma unroll
+        for (int k = 0; k < VB; ++k)
+            if (on[k]) VRec<VP>::store(rout + (unsigned)i * rstride, cs, il_vec<VP, VB>(t, T, k), o[k]);
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -965,7 +982,8 @@ template <int VP, int WF, int VB, bool ONLYX = false> cudaError_t step_il_launch
     int spb = a.tile[0] > 0 ? a.tile[0] : il_spb(tx, occ ? 128 : a.threads);
     spb = std::max(1, std::min(spb, cap / tx));
     spb = std::min(spb, a.g.hx);  // a strip never spans more than one row
-    const bool packed = (a.tile[1] == 2 || a.tile[1] == 3) && a.active == nullptr && a.alphaf && VP != P_F64;
+    // the packed kernel also serves slot batches (active table); the other staged forms do not
+    const bool packed = (a.tile[1] == 2 || (a.tile[1] == 3 && a.active == nullptr)) && a.alphaf && VP != P_F64;
     const bool staged = a.tile[1] > 0 && a.active == nullptr && a.alphaf;
     constexpr int kPackB = 6 * 9 * 16;  // W packs per site of the packed kernel
     // shared memory within the default dynamic limit (48 KB)
@@ -978,20 +996,23 @@ template <int VP, int WF, int VB, bool ONLYX = false> cudaError_t step_il_launch
     dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
     if constexpr (ONLYX) {
-        if (!packed || a.tile[1] != 2) return cudaErrorNotSupported;
+        if (!packed || a.tile[1] != 2 || a.active) return cudaErrorNotSupported;
         k_step_ilx<VP, WF, VB, false><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha, a.alphaf,
-                                                                               a.g, a.nvec);
+                                                                               nullptr, a.g, a.nvec);
         return cudaGetLastError();
     } else {
     if (packed) {
         // packed FP32 pairs with W packs in shared memory; 3 = all records requested up front
         if constexpr (VP != P_F64) {
-            if (a.tile[1] == 3)
+            if (a.active)
+                k_step_ilx<VP, WF, VB, false, true><<<grid, block, kPackB * spb, a.stream>>>(
+                    a.W, a.in, a.out, a.alpha, a.alphaf, a.active, a.g, a.nvec);
+            else if (a.tile[1] == 3)
                 k_step_ilx<VP, WF, VB, true><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha,
-                                                                                      a.alphaf, a.g, a.nvec);
+                                                                                      a.alphaf, nullptr, a.g, a.nvec);
             else
                 k_step_ilx<VP, WF, VB, false><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha,
-                                                                                       a.alphaf, a.g, a.nvec);
+                                                                                       a.alphaf, nullptr, a.g, a.nvec);
         }
     } else if (staged && a.tile[1] == 4 && VP != P_F64) {
         // W of the strip staged in shared memory as stored, packed FP32 pair FMAs

@@ -65,7 +65,8 @@ struct Batch {
     int *d_active = nullptr;
     double *h_alpha = nullptr;
     int *h_active = nullptr;
-    size_t tab_bytes = 0;
+    size_t tab_bytes = 0;    // one K x S table of 8-byte entries
+    size_t alpha_bytes = 0;  // the alpha table: FP64 entries, then the same rounded to FP32
     int cur = 0;
     std::vector<Job *> slot_job;
     std::vector<int> slot_left;
@@ -116,7 +117,7 @@ void destroy_batch(tls_ctx *ctx, Batch *b)
         if (g) cudaGraphExecDestroy(g);
     dev_free(ctx, b->buf[0], b->buf_bytes);
     dev_free(ctx, b->buf[1], b->buf_bytes);
-    dev_free(ctx, b->d_alpha, b->tab_bytes);
+    dev_free(ctx, b->d_alpha, b->alpha_bytes);
     dev_free(ctx, b->d_active, b->tab_bytes);
     if (b->h_alpha) cudaFreeHost(b->h_alpha);
     if (b->h_active) cudaFreeHost(b->h_active);
@@ -127,7 +128,7 @@ size_t batch_bytes(const Gauge &gg, int storage, int timeslice, int S, int K)
 {
     const int nsl = timeslice < 0 ? gg.L[3] : 1;
     const int64_t vs = (int64_t)nsl * 8 * gg.g.Ps * vfmt_bytes(storage);
-    return 2 * (size_t)vs * S + 2 * (size_t)K * S * 8;
+    return 2 * (size_t)vs * S + 2 * (size_t)K * S * 8 + (size_t)K * S * 4;
 }
 
 tls_status make_batch(tls_ctx *ctx, Server *sv, const BatchKey &key, const Gauge &gg, Batch **out)
@@ -143,11 +144,12 @@ tls_status make_batch(tls_ctx *ctx, Server *sv, const BatchKey &key, const Gauge
     b->vs = (int64_t)b->nblk * gg.g.Ps * vfmt_bytes(key.storage);
     b->buf_bytes = (size_t)b->vs * b->S;
     b->tab_bytes = (size_t)b->K * b->S * 8;
+    b->alpha_bytes = b->tab_bytes + (size_t)b->K * b->S * 4;
     tls_status s = dev_alloc(ctx, (void **)&b->buf[0], b->buf_bytes, "serve: batch buffer A");
     if (s == TLS_OK) s = dev_alloc(ctx, (void **)&b->buf[1], b->buf_bytes, "serve: batch buffer B");
-    if (s == TLS_OK) s = dev_alloc(ctx, (void **)&b->d_alpha, b->tab_bytes, "serve: alpha table");
+    if (s == TLS_OK) s = dev_alloc(ctx, (void **)&b->d_alpha, b->alpha_bytes, "serve: alpha table");
     if (s == TLS_OK) s = dev_alloc(ctx, (void **)&b->d_active, b->tab_bytes, "serve: active table");
-    if (s == TLS_OK && cudaMallocHost(&b->h_alpha, b->tab_bytes) != cudaSuccess) s = fail(TLS_ERR_NOMEM, "serve: pinned table");
+    if (s == TLS_OK && cudaMallocHost(&b->h_alpha, b->alpha_bytes) != cudaSuccess) s = fail(TLS_ERR_NOMEM, "serve: pinned table");
     if (s == TLS_OK && cudaMallocHost(&b->h_active, b->tab_bytes) != cudaSuccess) s = fail(TLS_ERR_NOMEM, "serve: pinned table");
     if (s == TLS_OK && cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
         s = fail(TLS_ERR_CUDA, "serve: stream");
@@ -297,7 +299,9 @@ cudaError_t launch_round(tls_ctx *ctx, Server *sv, Batch *b)
             b->h_active[j * b->S + s] = on ? 1 : 0;
             b->h_alpha[j * b->S + s] = on ? b->slot_alpha[s] : 0.0;
         }
-    cudaError_t e = cudaMemcpyAsync(b->d_alpha, b->h_alpha, b->tab_bytes, cudaMemcpyHostToDevice, b->stream);
+    float *h_alphaf = reinterpret_cast<float *>(b->h_alpha + (size_t)b->K * b->S);
+    for (size_t k = 0; k < (size_t)b->K * b->S; ++k) h_alphaf[k] = (float)b->h_alpha[k];  // round to nearest
+    cudaError_t e = cudaMemcpyAsync(b->d_alpha, b->h_alpha, b->alpha_bytes, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_active, b->h_active, b->tab_bytes, cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess) return e;
     StepArgs sa{};
@@ -310,12 +314,16 @@ cudaError_t launch_round(tls_ctx *ctx, Server *sv, Batch *b)
     sa.prec_in = sa.prec_out = b->key.storage;
     sa.vb = b->vb;
     sa.threads = 128;
+    // the packed FP32 pair kernel (W broadcast pairs in shared memory); FP64 batches use the plain one
+    if (b->key.storage != TLS_F64) sa.tile[1] = 2;
+    const float *d_alphaf = reinterpret_cast<const float *>(b->d_alpha + (size_t)b->K * b->S);
     sa.stream = b->stream;
     auto issue = [&]() -> cudaError_t {
         for (int j = 0; j < b->K; ++j) {
             sa.in = b->buf[(b->cur + j) & 1];
             sa.out = b->buf[(b->cur + j + 1) & 1];
             sa.alpha = b->d_alpha + (size_t)j * b->S;
+            sa.alphaf = d_alphaf + (size_t)j * b->S;
             sa.active = b->d_active + (size_t)j * b->S;
             cudaError_t r = launch_step_il(sa);
             if (r != cudaSuccess) return r;
