@@ -771,7 +771,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     cudaError_t e = cudaSuccess;
     int64_t launches = 0, iter_launches = 0;
     const bool prof = ctx->profiling;
-    float t_pack = 0, t_iter = 0, t_unpack = 0, t_h2d = 0, t_d2h = 0;
+    float t_pack = 0, t_iter = 0, t_unpack = 0, t_h2d = 0;
     // Phase timing: events on the launch stream, accumulated per vector group.
     auto mark = [&](int k) {
         if (prof) cudaEventRecord(ctx->ev[k], st);
