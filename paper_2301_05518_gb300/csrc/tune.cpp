@@ -42,6 +42,9 @@ std::vector<Cand> candidates(int nvec, int storage, bool rows, bool onchip)
                     c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 2, 0}});
                     c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 4, 0}});  // W as stored, packed FMAs
                 }
+        if (storage != TLS_F64)  // packed kernel with explicit strip lengths
+            for (int spb : {4, 8, 32})
+                if (spb * tx <= 256) c.push_back({TLS_KERNEL_MRHS, vb, 256, {spb, 2, 0}});
         if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0, {0, 0, 0}});
     }
     if (storage == TLS_F32 && G % 8 == 0)  // eight FP32 vectors per thread, packed kernel
