@@ -138,7 +138,8 @@ def test_busy_gauge_cannot_be_freed(T):
         gid, U = _gauge(T, ctx, dims, 47)
         ctx.serve_start(max_slots=4)
         x = synth.gaussian_vectors(dims, 1, 12, dtype=torch.complex64).cuda()
-        j = ctx.serve_submit(gid, x, T.TLS_F32, 1, 2000, 100.0)
+        # long enough (a few seconds) that the job is still in its batch when free_gauge runs
+        j = ctx.serve_submit(gid, x, T.TLS_F32, 1, 100000, 5000.0)
         with pytest.raises(T.TLSError) as e:
             ctx.free_gauge(gid)
         assert e.value.status == T.TLS_ERR_STATE
