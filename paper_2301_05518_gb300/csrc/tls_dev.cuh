@@ -370,21 +370,28 @@ template <typename H> struct VFmtH {
     template <bool CG> static __device__ __forceinline__ void load(const char *blk, int64_t, int i, cpx<float> v[3])
     {
         uint4 a = vld<CG>(reinterpret_cast<const uint4 *>(blk) + i);
-        float s = __uint_as_float(a.w);
-        float2 f0 = H2<H>::to2(a.x), f1 = H2<H>::to2(a.y), f2 = H2<H>::to2(a.z);
-        v[0].re = f0.x * s; v[0].im = f0.y * s;
-        v[1].re = f1.x * s; v[1].im = f1.y * s;
-        v[2].re = f2.x * s; v[2].im = f2.y * s;
+        const float s = __uint_as_float(a.w);
+        const float2 s2 = make_float2(s, s);
+        // packed FP32 multiplies: each lane rounds exactly as f * s
+        const float2 f0 = __fmul2_rn(H2<H>::to2(a.x), s2), f1 = __fmul2_rn(H2<H>::to2(a.y), s2),
+                     f2 = __fmul2_rn(H2<H>::to2(a.z), s2);
+        v[0].re = f0.x; v[0].im = f0.y;
+        v[1].re = f1.x; v[1].im = f1.y;
+        v[2].re = f2.x; v[2].im = f2.y;
     }
     template <bool CG> static __device__ __forceinline__ void store(char *blk, int64_t, int i, const cpx<float> v[3])
     {
         float m = fmaxf(fmaxf(fmaxf(fabsf(v[0].re), fabsf(v[0].im)), fmaxf(fabsf(v[1].re), fabsf(v[1].im))),
                         fmaxf(fabsf(v[2].re), fabsf(v[2].im)));
-        float inv = m > 0.0f ? 1.0f / m : 0.0f;
+        const float inv = m > 0.0f ? 1.0f / m : 0.0f;
+        const float2 i2 = make_float2(inv, inv);
+        const float2 q0 = __fmul2_rn(make_float2(v[0].re, v[0].im), i2);
+        const float2 q1 = __fmul2_rn(make_float2(v[1].re, v[1].im), i2);
+        const float2 q2 = __fmul2_rn(make_float2(v[2].re, v[2].im), i2);
         uint4 a;
-        a.x = H2<H>::from2(v[0].re * inv, v[0].im * inv);
-        a.y = H2<H>::from2(v[1].re * inv, v[1].im * inv);
-        a.z = H2<H>::from2(v[2].re * inv, v[2].im * inv);
+        a.x = H2<H>::from2(q0.x, q0.y);
+        a.y = H2<H>::from2(q1.x, q1.y);
+        a.z = H2<H>::from2(q2.x, q2.y);
         a.w = __float_as_uint(m);
         vst<CG>(reinterpret_cast<uint4 *>(blk) + i, a);
     }
