@@ -381,6 +381,37 @@ def sink_run(T, ctx, device, stream, hbm_peak):
             "ms_per_step": p["ms_iter"] / N, "gbs": gbs, "frac": gbs / hbm_peak, "kernel": best}
 
 
+def large_mrhs_run(T, ctx, device, stream, hbm_peak):
+    """48^3x64 Haar links, Gaussian batches of 12/24/48/96 vectors, N = 40:
+    autotuned smearing time per batch size and storage (FP32, FP16 + scale)."""
+    import torch
+    from paper_2301_05518_gb300 import synth, workloads
+    w = workloads.LARGE_MRHS
+    dims, N, sigma = w["dims"], w["N"], w["sigma"]
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    U = synth.gauge_haar(dims, w["gauge_seed"], nd=4, device=device)
+    gid = ctx.load_gauge(U, 4, dims, stream=stream)
+    ctx.build_twolink(gid, T.TLS_F32, T.TLS_R18, keep_U=0, stream=stream)
+    del U
+    out = []
+    for nvec in w["batches"]:
+        x0 = synth.gaussian_vectors(dims, nvec, w["vec_seed"], dtype=torch.complex64, device=device)
+        for name, st, vby in (("f32", T.TLS_F32, 48), ("f16", T.TLS_F16, 32)):
+            best, _ = ctx.autotune(gid, nvec, st, T.TLS_ALL_T, steps=3)
+            x = x0.clone()
+            ctx.smear(gid, x, T.TLS_F32, nvec, N, sigma, storage=st, stream=stream)
+            p = ctx.get_profile()
+            ms = p["ms_iter"] / N
+            out.append({"nvec": nvec, "storage": name, "ms_per_step": ms,
+                        "algorithmic_gbs": V * (216 + vby * nvec) / (ms / 1e3) / 1e9,
+                        "vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3), "kernel": best})
+            del x
+        del x0
+        torch.cuda.empty_cache()
+    ctx.free_gauge(gid)
+    return {"workload": "48^3x64 Haar, Gaussian batches, N=40, W f32-18", "runs": out}
+
+
 def small_lattice_run(T, ctx, device, stream, hbm_peak):
     """16^3x32 (8^3 sublattice blocks), 24 corner walls, N = 80: the on-chip
     persistent form (each block's W and iterates in one CTA's shared memory)
@@ -590,6 +621,8 @@ def our_arm(args):
         extra["sink_smear"] = sink_run(T, ctx, local, stream, hbm_peak)
         torch.cuda.empty_cache()
         extra["small_lattice"] = small_lattice_run(T, ctx, local, stream, hbm_peak)
+        torch.cuda.empty_cache()
+        extra["large_mrhs"] = large_mrhs_run(T, ctx, local, stream, hbm_peak)
         torch.cuda.empty_cache()
         extra["serving"] = serving_run(T, local, n_closed=24, n_open=args.serve_jobs, time_cap_s=25.0,
                                        fp64_cap_s=10.0)
