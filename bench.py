@@ -606,7 +606,7 @@ def our_arm(args):
         extra["ape_smear"] = {"ms_per_step": p["ms_total"], "alpha": 0.5,
                               "site_links_per_s": 3 * V / (p["ms_total"] / 1e3)}
         if rank == 0 and ws >= 1:
-            # CPU baseline: the oracle on a bounded sample, on this box's host cores
+            # CPU baseline: the oracle on a bounded sample, on this machine's host cores
             Lx, Ly, Lz, Lt = dims
             nsl = 8
             Uh1 = U[:nsl].cpu().numpy()
