@@ -82,6 +82,8 @@ def kernel_symbol(kern_name: str, entry: dict) -> str:
     """CUDA kernel that a tune-table entry launches (the name ncu lists)."""
     if kern_name == "mrhs":
         tile = tuple(entry.get("tile", (0, 0, 0)))
+        if tile[1] == 5:
+            return "k_step_ilx_occ"
         if tile[1] in (2, 3):
             return "k_step_ilx"
         if tile[1] in (1, 4):

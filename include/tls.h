@@ -276,7 +276,9 @@ typedef struct {
                             /* packed FP32 pair FMAs (not FP64), tile[1] = 3   */
                             /* like 2 with all vector loads issued up front,   */
                             /* tile[1] = 4 stages W as stored and applies it   */
-                            /* with packed FP32 pair FMAs; tile[2] unused      */
+                            /* with packed FP32 pair FMAs, tile[1] = 5 is 2    */
+                            /* held to 56 registers in CTAs of <= 96 threads;  */
+                            /* tile[2] unused                                  */
     double ms_per_step;     /* measured time of one smearing step              */
 } tls_tune_entry;
 

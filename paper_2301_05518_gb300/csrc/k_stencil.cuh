@@ -469,11 +469,11 @@ __global__ void __launch_bounds__(256) k_step_ilw(const char *__restrict__ W, co
 // results are bitwise equal to every other kernel.  Arithmetic in FP32 (FP32
 // and 16-bit storage).
 // --------------------------------------------------------------------------
-template <int VP, int WF, int VB, bool PRE, bool ACT = false>
-__global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, const char *__restrict__ in,
-                                                  char *__restrict__ out, const double *__restrict__ alpha,
-                                                  const float *__restrict__ alphaf, const int *__restrict__ active,
-                                                  SubGeom g, int nvec)
+template <int VP, int WF, int VB, bool PRE, bool ACT>
+__device__ __forceinline__ void ilx_body(const char *__restrict__ W, const char *__restrict__ in,
+                                         char *__restrict__ out, const double *__restrict__ alpha,
+                                         const float *__restrict__ alphaf, const int *__restrict__ active,
+                                         const SubGeom &g, int nvec)
 {
     static_assert(VP != P_F64, "packed FP32 pairs only");
     constexpr int WB = wfmt_bytes(WF);
@@ -622,6 +622,24 @@ __global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, co
         for (int k = 0; k < VB; ++k)
             if (on[k]) VRec<VP>::store(rout + (unsigned)i * rstride, cs, il_vec<VP, VB>(t, T, k), o[k]);
     }
+}
+
+template <int VP, int WF, int VB, bool PRE, bool ACT = false>
+__global__ void __launch_bounds__(256) k_step_ilx(const char *__restrict__ W, const char *__restrict__ in,
+                                                  char *__restrict__ out, const double *__restrict__ alpha,
+                                                  const float *__restrict__ alphaf, const int *__restrict__ active,
+                                                  SubGeom g, int nvec)
+{
+    ilx_body<VP, WF, VB, PRE, ACT>(W, in, out, alpha, alphaf, active, g, nvec);
+}
+
+// The same held to 56 registers in CTAs of at most 96 threads (12 CTAs per SM).
+template <int VP, int WF, int VB>
+__global__ void __launch_bounds__(96, 12) k_step_ilx_occ(const char *__restrict__ W, const char *__restrict__ in,
+                                                         char *__restrict__ out, const double *__restrict__ alpha,
+                                                         const float *__restrict__ alphaf, SubGeom g, int nvec)
+{
+    ilx_body<VP, WF, VB, false, false>(W, in, out, alpha, alphaf, nullptr, g, nvec);
 }
 
 // --------------------------------------------------------------------------
@@ -978,12 +996,14 @@ template <int VP, int WF, int VB, bool ONLYX = false> cudaError_t step_il_launch
     // a strip of spb consecutive x' per CTA; tile[0] > 0 sets spb explicitly
     // threads = -128 selects the 64-register variant (CTAs of <= 128 threads)
     const bool occ = a.threads < 0;
-    const int cap = occ ? 128 : 256;
+    const bool xocc = a.tile[1] == 5;  // packed kernel, register-capped CTAs of <= 96 threads
+    const int cap = xocc ? 96 : occ ? 128 : 256;
     int spb = a.tile[0] > 0 ? a.tile[0] : il_spb(tx, occ ? 128 : a.threads);
     spb = std::max(1, std::min(spb, cap / tx));
     spb = std::min(spb, a.g.hx);  // a strip never spans more than one row
     // the packed kernel also serves slot batches (active table); the other staged forms do not
-    const bool packed = (a.tile[1] == 2 || (a.tile[1] == 3 && a.active == nullptr)) && a.alphaf && VP != P_F64;
+    const bool packed = (a.tile[1] == 2 || ((a.tile[1] == 3 || a.tile[1] == 5) && a.active == nullptr)) && a.alphaf &&
+                        VP != P_F64;
     const bool staged = a.tile[1] > 0 && a.active == nullptr && a.alphaf;
     constexpr int kPackB = 6 * 9 * 16;  // W packs per site of the packed kernel
     // shared memory within the default dynamic limit (48 KB)
@@ -1010,6 +1030,9 @@ template <int VP, int WF, int VB, bool ONLYX = false> cudaError_t step_il_launch
             else if (a.tile[1] == 3)
                 k_step_ilx<VP, WF, VB, true><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha,
                                                                                       a.alphaf, nullptr, a.g, a.nvec);
+            else if (a.tile[1] == 5)
+                k_step_ilx_occ<VP, WF, VB><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha,
+                                                                                      a.alphaf, a.g, a.nvec);
             else
                 k_step_ilx<VP, WF, VB, false><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha,
                                                                                        a.alphaf, nullptr, a.g, a.nvec);

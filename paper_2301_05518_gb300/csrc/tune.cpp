@@ -42,6 +42,8 @@ std::vector<Cand> candidates(int nvec, int storage, bool rows, bool onchip)
                     c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 2, 0}});
                     c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 4, 0}});  // W as stored, packed FMAs
                 }
+        if (storage != TLS_F64 && tx <= 96)  // packed kernel, register-capped CTAs of <= 96 threads
+            c.push_back({TLS_KERNEL_MRHS, vb, 96, {0, 5, 0}});
         if (storage != TLS_F64)  // packed kernel with explicit strip lengths
             for (int spb : {4, 8, 32})
                 if (spb * tx <= 256) c.push_back({TLS_KERNEL_MRHS, vb, 256, {spb, 2, 0}});

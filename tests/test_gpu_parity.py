@@ -427,7 +427,8 @@ def test_rows_kernel_at_headline_shape_sampled(ctx, T):
                                              ((7, 2, 0), 1, "F16"), ((0, 3, 0), 2, "F32"), ((5, 3, 0), 4, "F16"),
                                              ((3, 3, 0), 1, "F32"), ((0, 3, 0), 4, "BF16"), ((0, 4, 0), 2, "F32"),
                                              ((5, 4, 0), 4, "F16"), ((3, 4, 0), 1, "BF16"), ((0, 4, 0), 4, "F32"),
-                                             ((0, 2, 0), 8, "F32"), ((3, 2, 0), 8, "F32")])
+                                             ((0, 2, 0), 8, "F32"), ((3, 2, 0), 8, "F32"), ((0, 5, 0), 4, "F32"),
+                                             ((0, 5, 0), 2, "F16"), ((5, 5, 0), 1, "BF16")])
 @pytest.mark.parametrize("recon", [18, 12])
 def test_interleaved_strips_bitwise_equal_single(ctx, T, tile, vb, storage, recon):
     """Strip lengths (some not dividing hx), W staged in shared memory (tile[1] = 1) and the
