@@ -79,3 +79,20 @@ def test_struct_sizes_match_header(libpath):
     assert sizes == [ctypes.sizeof(tls.tls_profile), ctypes.sizeof(tls.tls_serve_opts),
                      ctypes.sizeof(tls.tls_job), ctypes.sizeof(tls.tls_job_result),
                      ctypes.sizeof(tls.tls_tune_entry)]
+
+
+def test_binding_argument_counts_match_header(libpath):
+    """Every ctypes prototype has as many arguments as its declaration in tls.h."""
+    from paper_2301_05518_gb300 import tls
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    decls = re.findall(r"\b(tls_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S)
+    assert decls
+    checked = 0
+    for name, params in decls:
+        params = params.strip()
+        n = 0 if params in ("", "void") else len([p for p in params.split(",") if p.strip()])
+        fn = getattr(tls.lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+        checked += 1
+    assert checked == len(_declared())
