@@ -124,6 +124,16 @@ def workload(small, lattice=None):
     return w
 
 
+def workload_config(w, storage: str, ws: int) -> dict:
+    """The `config` of the JSON line, the same for both arms: what the workload is."""
+    return {"workload": w["name"], "lattice": list(w["dims"]), "nvec": w["nvec"], "N": w["N"],
+            "sigma": w["sigma"], "links": "near-unit exp(i %g H), seed %d" % (w["eps"], w["gauge_seed"]),
+            "storage": storage, "w_format": "f32-18 (built in f64)",
+            "l2": "inputs larger than L2 (no flush)",
+            "step": "load_gauge + build_twolink + smear(%d vecs, N=%d, all slices) + free_gauge" % (w["nvec"], w["N"]),
+            "parallelism": "replicas x%d" % ws}
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region (clocks and throttle reasons)."""
 
@@ -225,8 +235,7 @@ def reference_arm(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["name"], "lattice": list(w["dims"]), "nvec": w["nvec"], "N": w["N"],
-                   "sigma": w["sigma"]},
+        "config": workload_config(w, args.storage, ws),
         "cpu_baseline": {"value": vec_per_s, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": vec_per_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -547,12 +556,7 @@ def our_arm(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": w["name"], "lattice": list(dims), "nvec": nvec, "N": N, "sigma": sigma,
-                   "links": "near-unit exp(i 0.2 H), seed %d" % w["gauge_seed"],
-                   "storage": args.storage, "w_format": "f32-18 (built in f64)", "kernel": kern_name,
-                   "l2": "inputs larger than L2 (no flush)",
-                   "step": "load_gauge + build_twolink + smear(24 vecs, N=80, all slices) + free_gauge",
-                   "parallelism": "replicas x%d" % ws},
+        "config": workload_config(w, args.storage, ws),
         "roofline": roof,
         "gpu_launches": launches_per_step[0] * args.steps,
         "clocks": clk,
