@@ -500,3 +500,43 @@ def test_ape_output_is_su3():
     A = oracle.ape_smear(U, 0.5, 3)
     assert np.abs(A @ np.conj(np.swapaxes(A, -1, -2)) - np.eye(3)).max() < 1e-13
     assert np.abs(np.linalg.det(A) - 1).max() < 1e-13
+
+
+# --------------------------------------------------------------------------- input recipe
+# The seeded stand-ins for the paper's configurations and sources (Sec. 3-4, 6).
+@pytest.mark.parametrize("kind", ["near", "haar"])
+def test_inputs_links_are_su3(kind):
+    U = _gauge((4, 6, 4, 2), 81, kind, eps=0.3, nd=4)
+    eye = np.eye(3)
+    assert np.abs(U @ np.conj(np.swapaxes(U, -1, -2)) - eye).max() < 1e-13
+    assert np.abs(np.linalg.det(U) - 1).max() < 1e-13
+
+
+def test_inputs_near_unit_links_scale_with_eps():
+    """exp(i eps H) with unit-variance Gell-Mann coefficients: |U - 1| grows like eps."""
+    d1 = np.abs(_gauge((4, 4, 4, 1), 82, "near", eps=0.05) - np.eye(3)).mean()
+    d2 = np.abs(_gauge((4, 4, 4, 1), 82, "near", eps=0.10) - np.eye(3)).mean()
+    assert 1.8 < d2 / d1 < 2.2
+
+
+def test_inputs_corner_walls():
+    """24 vectors = 3 colours x 8 corners on slice 0; each one sublattice, unit colour vector."""
+    dims = (6, 4, 8, 3)
+    src = synth.corner_wall_sources(dims).numpy()
+    assert src.shape == (24,) + (3, 8, 4, 6, 3)
+    for c in range(8):
+        for a in range(3):
+            v = src[3 * c + a]
+            assert np.array_equal(v[1:], np.zeros_like(v[1:]))  # only t = 0
+            mask = sublattice_mask(dims, c)                     # sites of corner c on a slice
+            assert np.array_equal(v[0][..., a] != 0, mask)
+            assert np.all(v[0][mask][:, a] == 1) and np.all(np.delete(v[0][mask], a, axis=-1) == 0)
+    assert src.sum() == 3 * dims[0] * dims[1] * dims[2]  # every site of slice 0 once per colour
+
+
+def test_inputs_gaussian_vectors_moments():
+    x = synth.gaussian_vectors((8, 8, 8, 2), 4, 83).numpy()
+    assert abs(x.real.mean()) < 0.02 and abs(x.imag.mean()) < 0.02
+    assert abs(x.real.var() - 1) < 0.03 and abs(x.imag.var() - 1) < 0.03
+    only = synth.gaussian_vectors((8, 8, 8, 3), 2, 83, t=1).numpy()
+    assert np.count_nonzero(only[:, 0]) == 0 and np.count_nonzero(only[:, 2]) == 0
