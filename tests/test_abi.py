@@ -96,3 +96,17 @@ def test_binding_argument_counts_match_header(libpath):
         assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
         checked += 1
     assert checked == len(_declared())
+
+
+def test_binding_without_library_fails_loudly(tmp_path):
+    """No CPU fallback: a package copy without libtls.so refuses to import."""
+    import shutil
+    import sys
+    pkg = os.path.join(ROOT, "paper_2301_05518_gb300")
+    dst = tmp_path / "paper_2301_05518_gb300"
+    shutil.copytree(pkg, dst, ignore=shutil.ignore_patterns("*.so", "_build", "__pycache__"))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "try:\n    import paper_2301_05518_gb300.tls\nexcept ImportError as e:\n    print('refused:', e)\n"
+            "else:\n    print('imported')\n") % str(tmp_path)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=str(tmp_path)).stdout
+    assert out.startswith("refused:"), out
