@@ -48,12 +48,13 @@ def parse():
     ap.add_argument("--kernel", default="auto", choices=["auto", "single", "mrhs", "persistent", "rows", "zm"])
     ap.add_argument("--small", action="store_true", help="16^3x8 lattice, for quick checks only")
     ap.add_argument("--lattice", default=None, help="Lx,Ly,Lz,Lt override (profiling cases)")
+    ap.add_argument("--nvec", type=int, default=0, help="smear only the first n corner walls (profiling cases)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (planner default)")
     ap.add_argument("--vb", type=int, default=0, help="with --kernel: vectors per thread (profiling cases)")
     ap.add_argument("--threads", type=int, default=0, help="with --kernel: threads per CTA (profiling cases)")
     ap.add_argument("--tile", default="0,0,0", help="with --kernel: tile entry of the tune table")
     ap.add_argument("--serving", action="store_true", help="run only the serving benchmark (longer)")
-    ap.add_argument("--serve-jobs", type=int, default=60, help="open-loop jobs of the serving run")
+    ap.add_argument("--serve-jobs", type=int, default=500, help="open-loop jobs of the serving run")
     ap.add_argument("--no-extra", action="store_true", help="skip e2e, cpu baseline and side measurements")
     return ap.parse_args()
 
@@ -78,10 +79,21 @@ PROFILED_TRAFFIC_PER_SITE = {
 }
 
 
+# FP64 flops of one APE link update, counted from its formula: 4 staples of two
+# 3x3 complex products (2 x 27 complex multiply-adds, 8 flops each), the mix
+# (18 reals x 2 flops x 5 terms), then the polar projection: per Newton step
+# a 3x3 complex inverse by cofactors (9 2x2 cofactor determinants of 2 complex
+# products each, the determinant, 9 divisions: ~ 250 flops) and the average
+# (36), three steps counted; the determinant phase (~ 60).
+APE_FLOPS_PER_LINK = 4 * 2 * 27 * 8 + 18 * 2 * 5 + 3 * (250 + 36) + 60
+
+
 def kernel_symbol(kern_name: str, entry: dict) -> str:
     """CUDA kernel that a tune-table entry launches (the name ncu lists)."""
     if kern_name == "mrhs":
         tile = tuple(entry.get("tile", (0, 0, 0)))
+        if tile[1] in (6, 7):
+            return "k_step_ilt"
         if tile[1] == 5:
             return "k_step_ilx_occ"
         if tile[1] in (2, 3):
@@ -113,14 +125,16 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def workload(small, lattice=None):
+def workload(small, lattice=None, nvec=0):
     from paper_2301_05518_gb300 import workloads
     w = dict(workloads.HEADLINE)
+    if nvec:
+        w.update(nvec=nvec)
     if small:
         w.update(dims=(16, 16, 16, 8), name="16^3x8 24 corner-wall sources N=80 (quick check)")
     if lattice:
         dims = tuple(int(x) for x in lattice.split(","))
-        w.update(dims=dims, name="%dx%dx%dx%d 24 corner-wall sources N=80 (profiling case)" % dims)
+        w.update(dims=dims, name="%dx%dx%dx%d %d corner-wall sources N=80 (profiling case)" % (dims + (w["nvec"],)))
     return w
 
 
@@ -187,6 +201,8 @@ def make_inputs(w, device):
     dims = w["dims"]
     U = synth.gauge_near_unit(dims, w["eps"], w["gauge_seed"], nd=4, device=device)
     vecs = synth.corner_wall_sources(dims, t=0, dtype=torch.complex64, device=device)
+    if w["nvec"] < vecs.shape[0]:
+        vecs = vecs[:w["nvec"]].contiguous()
     return U, vecs
 
 
@@ -204,6 +220,69 @@ def cpu_sample(w, U_host_slices, nsl, n_steps):
     return dt, oracle.threads()
 
 
+def oracle_rel_err(U_slices, src, got, N, sigma):
+    """Largest relative L2 error over the vectors of `got` against the FP64 oracle
+    smearing `src` (host arrays [nvec, k, Lz, Ly, Lx, 3]) on the k slices U_slices."""
+    import numpy as np
+    import oracle
+    W = oracle.twolink(np.ascontiguousarray(U_slices))
+    want = oracle.smear(W, np.ascontiguousarray(src).astype(np.complex128), N, sigma)
+    got = np.asarray(got).astype(np.complex128)
+    return max(float(np.linalg.norm(got[v] - want[v]) / np.linalg.norm(want[v])) for v in range(want.shape[0]))
+
+
+def config01_run(T, ctx, stream):
+    """The two small workloads, each smeared by the plain one-vector-per-launch
+    form and checked against the FP64 oracle:
+      8^3x16, exp(i 0.3 H) links, colour-0 point source at the origin, N = 10 on
+      slice 0, FP64;
+      32^3x64, exp(i 0.3 H) links, 3 colour point sources + 3 Gaussian vectors,
+      N = 40 on every slice, FP64 and FP32 storage (error on 4 sampled slices)."""
+    import torch
+    from paper_2301_05518_gb300 import synth, workloads
+    out = {}
+    w = workloads.SMALL_POINT
+    dims = w["dims"]
+    U = synth.gauge_near_unit(dims, w["eps"], w["gauge_seed"], nd=4, device="cuda")
+    x = synth.point_sources(dims, [(0, 0, 0, 0)], [0], device="cuda")
+    src = x.cpu().numpy()
+    gid = ctx.load_gauge(U, 4, dims, stream=stream)
+    ctx.build_twolink(gid, T.TLS_F64, T.TLS_R18, keep_U=0, stream=stream)
+    ctx.smear(gid, x, T.TLS_F64, 1, w["N"], w["sigma"], timeslice=0, storage=T.TLS_F64,
+              kernel=T.TLS_KERNEL_SINGLE, stream=stream)
+    p = ctx.get_profile()
+    ctx.free_gauge(gid)
+    err = oracle_rel_err(U[0:1].cpu().numpy(), src[:, 0:1], x[:, 0:1].cpu().numpy(), w["N"], w["sigma"])
+    out["small_point"] = {"workload": "8^3x16 point source, slice 0, N=10, FP64, one vector per launch",
+                          "ms": p["ms_total"], "max_rel_l2": err, "tolerance": 1e-13}
+    w = workloads.MEDIUM_MIXED
+    dims = w["dims"]
+    U = synth.gauge_near_unit(dims, w["eps"], w["gauge_seed"], nd=4, device="cuda")
+    pts = synth.point_sources(dims, [(0, 0, 0, 0)] * 3, [0, 1, 2], device="cuda")
+    gv = synth.gaussian_vectors(dims, 3, w["vec_seed"], device="cuda")
+    x0 = torch.cat([pts, gv])
+    sl = [0, 21, 42, 63]
+    Uh = U[sl].cpu().numpy()
+    srch = x0[:, sl].cpu().numpy()
+    gid = ctx.load_gauge(U, 4, dims, stream=stream)
+    res = {}
+    for name, st in (("f64", T.TLS_F64), ("f32", T.TLS_F32)):
+        ctx.build_twolink(gid, st, T.TLS_R18, keep_U=1, stream=stream)
+        x = x0.clone() if st == T.TLS_F64 else x0.to(torch.complex64)
+        V = dims[0] * dims[1] * dims[2] * dims[3]
+        ctx.smear(gid, x, st, 6, w["N"], w["sigma"], storage=st, kernel=T.TLS_KERNEL_SINGLE, stream=stream)
+        p = ctx.get_profile()
+        err = oracle_rel_err(Uh, srch, x[:, sl].cpu().numpy(), w["N"], w["sigma"])
+        ms = p["ms_iter"] / (w["N"] * 6)
+        res[name] = {"vectors_per_s": 6 / (p["ms_total"] / 1e3), "ms_per_step_per_vector": ms,
+                     "gbs": p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9, "max_rel_l2": err,
+                     "tolerance": 1e-13 if st == T.TLS_F64 else 2e-6 * w["N"], "sites": V}
+    ctx.free_gauge(gid)
+    out["medium_mixed"] = {"workload": "32^3x64 3 point + 3 Gaussian vectors, N=40, all slices, one vector "
+                                       "per launch; error on slices 0, 21, 42, 63", **res}
+    return out
+
+
 def reference_arm(args):
     """The FP64 CPU oracle on the host cores, a bounded sample per step."""
     ws, rank, local = dist_setup("gloo")
@@ -213,7 +292,7 @@ def reference_arm(args):
     import torch
     import oracle
     from paper_2301_05518_gb300 import synth
-    w = workload(args.small, args.lattice)
+    w = workload(args.small, args.lattice, args.nvec)
     oracle.build()
     Lx, Ly, Lz, Lt = w["dims"]
     nsl = 4
@@ -244,31 +323,41 @@ def reference_arm(args):
     return 0
 
 
-def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0):
+def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0, n_check=3):
     """Continuous-batching serving on resident gauge fields (Poisson arrivals).
 
     Phase 1 keeps 8 jobs in flight to measure the saturation rate X_sat
     (vectors/s); phase 2 submits n_open jobs at Poisson times with rate
-    0.7 * X_sat / E[nvec] and reports submit->result latency.  The same job
-    stream is then smeared by the plain FP64 one-vector-at-a-time form
-    (tls_smear, TLS_KERNEL_SINGLE, FP64 storage and W) for comparison.
+    0.7 * X_sat / E[nvec] and reports submit->result latency.  Each job's
+    vectors are drawn on a client stream of their own, and the client waits
+    for that stream only before it submits: the scheduler's batches run on
+    with no device-wide synchronisation in the submit path.  n_check jobs on
+    the 16^3x32 field are also smeared by the FP64 oracle (relative L2 error
+    per vector reported).  The same job stream is then smeared by the plain
+    FP64 one-vector-at-a-time form (tls_smear, TLS_KERNEL_SINGLE, FP64
+    storage and W) for comparison.
     """
     import threading
     import numpy as np
     import torch
+    import oracle
     from paper_2301_05518_gb300 import synth, workloads
     w = workloads.SERVING
     rng = np.random.default_rng(w["arrival_seed"])
     torch.manual_seed(w["vec_seed"])
     ctx = T.Context(device, hbm_cap_bytes=w["hbm_cap"])
     gids, gids64 = [], []
+    U_small = None
     for k, dims in enumerate(w["configs"]):
         U = synth.gauge_haar(dims, w["gauge_seed"] + k, nd=4, device="cuda")
+        if k == 0:
+            U_small = U.cpu().numpy()
         g = ctx.load_gauge(U, 4, dims)
         ctx.build_twolink(g, T.TLS_F32, T.TLS_R18, keep_U=0)
         gids.append(g)
         del U
     torch.cuda.synchronize()
+    client = torch.cuda.Stream()
 
     def spec():
         c = int(rng.integers(0, len(w["configs"])))
@@ -280,7 +369,10 @@ def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0):
 
     def vecs_for(c, nvec):
         Lx, Ly, Lz, Lt = w["configs"][c]
-        return torch.randn((nvec, Lt, Lz, Ly, Lx, 3), dtype=torch.complex64, device="cuda")
+        with torch.cuda.stream(client):
+            x = torch.randn((nvec, Lt, Lz, Ly, Lx, 3), dtype=torch.complex64, device="cuda")
+        client.synchronize()  # this client's stream only, not the scheduler's
+        return x
 
     ctx.serve_start(max_slots=48, steps_per_launch=4, use_graphs=1)
     # phase 1: closed loop
@@ -296,7 +388,6 @@ def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0):
                 break
             c, nvec, N, sig, st = sp
             x = vecs_for(c, nvec)
-            torch.cuda.synchronize()
             pending.append((ctx.serve_submit(gids[c], x, T.TLS_F32, nvec, N, sig, storage=st), x, nvec))
         if not pending:
             break
@@ -315,12 +406,15 @@ def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0):
     lam = 0.7 * x_sat / mean_nvec
     gaps = rng.exponential(1.0 / lam, size=n_open)
     results = []
+    checks = []
     lock = threading.Lock()
 
-    def waiter(j, nvec, keep):
+    def waiter(j, nvec, keep, check):
         r = ctx.serve_wait(j, 900)
         with lock:
             results.append((r, nvec))
+            if check is not None:
+                checks.append((check, keep.cpu().numpy()))
         del keep
 
     threads = []
@@ -329,12 +423,15 @@ def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0):
     for (c, nvec, N, sig, st), gap in zip(specs2, gaps):
         tnext += gap
         x = vecs_for(c, nvec)
-        torch.cuda.synchronize()
+        check = None
+        if c == 0 and len(threads) % 7 == 0 and sum(1 for t_ in threads if t_.check is not None) < n_check:
+            check = (x.cpu().numpy(), N, sig, st)
         now = time.perf_counter()
         if tnext > now:
             time.sleep(tnext - now)
         j = ctx.serve_submit(gids[c], x, T.TLS_F32, nvec, N, sig, storage=st)
-        th = threading.Thread(target=waiter, args=(j, nvec, x))
+        th = threading.Thread(target=waiter, args=(j, nvec, x, check))
+        th.check = check
         th.start()
         threads.append(th)
         if time.perf_counter() - start > time_cap_s:
@@ -348,8 +445,19 @@ def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0):
     out = {"workload": "Poisson jobs on resident 16^3x32, 32^3x64, 48^3x96 Haar fields; 1-24 vectors, "
                        "N 10-80, sigma/N 0.05-0.3, FP32/FP16 50:50, cap 120 GB",
            "x_sat_vectors_per_s": x_sat, "rate_jobs_per_s": lam, "jobs": len(results),
+           "jobs_planned": n_open,
            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
            "max_ms": float(lat.max()), "vectors_per_s": vec_total / span_s}
+    # sampled jobs against the FP64 oracle (relative L2 per vector)
+    if checks:
+        W_small = oracle.twolink(U_small)
+        errs = []
+        for (src, N, sig, st), got in checks:
+            want = oracle.smear(W_small, src.astype(np.complex128), N, sig)
+            e_ = max(float(np.linalg.norm(got[v] - want[v]) / np.linalg.norm(want[v])) for v in range(src.shape[0]))
+            errs.append({"storage": "f32" if st == T.TLS_F32 else "f16", "nvec": int(src.shape[0]), "N": N,
+                         "max_rel_l2": e_, "tolerance": 2e-6 * N if st == T.TLS_F32 else 5e-3})
+        out["oracle_check"] = errs
     # plain FP64 one-vector-at-a-time on the same stream (bounded by time)
     for k, dims in enumerate(w["configs"]):
         U = synth.gauge_haar(dims, w["gauge_seed"] + k, nd=4, device="cuda")
@@ -379,6 +487,9 @@ def sink_run(T, ctx, device, stream, hbm_peak):
     dims, nvec, N, sigma = w["dims"], w["nvec"], w["N"], w["sigma"]
     U = synth.gauge_near_unit(dims, w["eps"], w["gauge_seed"], nd=4, device=device)
     x = synth.gaussian_vectors(dims, nvec, w["vec_seed"], dtype=torch.complex64, device=device)
+    ts = 31
+    Uh = U[ts:ts + 1].cpu().numpy()
+    src = x[0:2, ts:ts + 1].cpu().numpy()
     gid = ctx.load_gauge(U, 4, dims, stream=stream)
     ctx.build_twolink(gid, T.TLS_F32, T.TLS_R18, keep_U=0, stream=stream)
     del U
@@ -386,66 +497,92 @@ def sink_run(T, ctx, device, stream, hbm_peak):
     ctx.smear(gid, x, T.TLS_F32, nvec, N, sigma, storage=T.TLS_F32, stream=stream)
     p = ctx.get_profile()
     ctx.free_gauge(gid)
+    err = oracle_rel_err(Uh, src, x[0:2, ts:ts + 1].cpu().numpy(), N, sigma)
     del x
     gbs = p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9
     return {"workload": w["name"], "vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3),
-            "ms_per_step": p["ms_iter"] / N, "gbs": gbs, "frac": gbs / hbm_peak, "kernel": best}
+            "ms_per_step": p["ms_iter"] / N, "gbs": gbs, "frac": gbs / hbm_peak, "kernel": best,
+            "max_rel_l2": err, "tolerance": 2e-6 * N, "error_sample": "vectors 0-1 on slice 31"}
 
 
 def large_mrhs_run(T, ctx, device, stream, hbm_peak):
-    """48^3x64 Haar links, Gaussian batches of 12/24/48/96 vectors, N = 40:
-    autotuned smearing time per batch size and storage (FP32, FP16 + scale)."""
+    """48^3x64 Haar links, Gaussian batches of 12/24/48/96 vectors, N = 40, autotuned:
+    storage FP32, FP16 and BF16 (+ per-site scale) with W f32-18 at every batch size;
+    W f32-12 and f32-8 (FP32 storage) and W f16-18 / f16-12 / bf16-18 (16-bit storage) at
+    24 vectors.  Each run states the error of two of its vectors on one sampled slice
+    against the FP64 oracle."""
     import torch
     from paper_2301_05518_gb300 import synth, workloads
     w = workloads.LARGE_MRHS
     dims, N, sigma = w["dims"], w["N"], w["sigma"]
     V = dims[0] * dims[1] * dims[2] * dims[3]
     U = synth.gauge_haar(dims, w["gauge_seed"], nd=4, device=device)
+    ts = 17
+    Uh = U[ts:ts + 1].cpu().numpy()
     gid = ctx.load_gauge(U, 4, dims, stream=stream)
-    ctx.build_twolink(gid, T.TLS_F32, T.TLS_R18, keep_U=0, stream=stream)
     del U
+    names = {T.TLS_F32: "f32", T.TLS_F16: "f16", T.TLS_BF16: "bf16"}
+    vby = {T.TLS_F32: 48, T.TLS_F16: 32, T.TLS_BF16: 32}
+    plan = [((T.TLS_F32, 18), [(n, st) for n in w["batches"] for st in (T.TLS_F32, T.TLS_F16, T.TLS_BF16)]),
+            ((T.TLS_F32, 12), [(24, T.TLS_F32)]), ((T.TLS_F32, 8), [(24, T.TLS_F32)]),
+            ((T.TLS_F16, 18), [(24, T.TLS_F16)]), ((T.TLS_F16, 12), [(24, T.TLS_F16)]),
+            ((T.TLS_BF16, 18), [(24, T.TLS_BF16)])]
+    wbytes = {(T.TLS_F32, 18): 216, (T.TLS_F32, 12): 144, (T.TLS_F32, 8): 96, (T.TLS_F16, 18): 108,
+              (T.TLS_F16, 12): 72, (T.TLS_BF16, 18): 108}
     out = []
-    for nvec in w["batches"]:
-        x0 = synth.gaussian_vectors(dims, nvec, w["vec_seed"], dtype=torch.complex64, device=device)
-        for name, st, vby in (("f32", T.TLS_F32, 48), ("f16", T.TLS_F16, 32)):
+    for (wp, rc), runs in plan:
+        ctx.build_twolink(gid, wp, rc, keep_U=1, stream=stream)
+        for nvec, st in runs:
+            x0 = synth.gaussian_vectors(dims, nvec, w["vec_seed"], dtype=torch.complex64, device=device)
+            src = x0[0:2, ts:ts + 1].cpu().numpy()
             best, _ = ctx.autotune(gid, nvec, st, T.TLS_ALL_T, steps=3)
             x = x0.clone()
             ctx.smear(gid, x, T.TLS_F32, nvec, N, sigma, storage=st, stream=stream)
             p = ctx.get_profile()
             ms = p["ms_iter"] / N
-            out.append({"nvec": nvec, "storage": name, "ms_per_step": ms,
-                        "algorithmic_gbs": V * (216 + vby * nvec) / (ms / 1e3) / 1e9,
-                        "vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3), "kernel": best})
-            del x
-        del x0
+            gbs = V * (wbytes[(wp, rc)] + vby[st] * nvec) / (ms / 1e3) / 1e9
+            err = oracle_rel_err(Uh, src, x[0:2, ts:ts + 1].cpu().numpy(), N, sigma)
+            out.append({"nvec": nvec, "storage": names[st], "w_format": "%s-%d" % (names[wp], rc),
+                        "ms_per_step": ms, "algorithmic_gbs": gbs, "frac": gbs / hbm_peak,
+                        "vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3), "kernel": best,
+                        "max_rel_l2": err, "tolerance": 2e-6 * N if st == T.TLS_F32 else 5e-3})
+            del x, x0
         torch.cuda.empty_cache()
     ctx.free_gauge(gid)
-    return {"workload": "48^3x64 Haar, Gaussian batches, N=40, W f32-18", "runs": out}
+    return {"workload": "48^3x64 Haar, Gaussian batches, N=40; error on slice 17, vectors 0-1", "runs": out}
 
 
 def small_lattice_run(T, ctx, device, stream, hbm_peak):
-    """16^3x32 (8^3 sublattice blocks), 24 corner walls, N = 80: the on-chip
-    persistent form (each block's W and iterates in one CTA's shared memory)
-    against the step-by-step kernels, all through the autotuner."""
+    """16^3x32 (8^3 sublattice blocks), 24 corner walls, N = 80: the autotuned
+    step kernel against the two persistent forms run explicitly -- on chip
+    (each block's W and iterates in one CTA's shared memory for all N steps)
+    and L2-resident groups with a grid barrier per step.  Effective GB/s counts
+    the algorithmic bytes of all N steps."""
     import torch
     from paper_2301_05518_gb300 import synth
     dims, nvec, N, sigma = (16, 16, 16, 32), 24, 80, 16.0
     U = synth.gauge_near_unit(dims, 0.2, 1006, nd=4, device=device)
-    x = synth.corner_wall_sources(dims, t=0, dtype=torch.complex64, device=device)
+    x0 = synth.corner_wall_sources(dims, t=0, dtype=torch.complex64, device=device)
     gid = ctx.load_gauge(U, 4, dims, stream=stream)
     ctx.build_twolink(gid, T.TLS_F32, T.TLS_R18, keep_U=0, stream=stream)
-    best, cands = ctx.autotune(gid, nvec, T.TLS_F32, T.TLS_ALL_T, steps=N)
-    ctx.smear(gid, x, T.TLS_F32, nvec, N, sigma, storage=T.TLS_F32, stream=stream)
-    p = ctx.get_profile()
-    ctx.free_gauge(gid)
-    onchip = [c for c in cands if c["kernel"] == T.TLS_KERNEL_PERSISTENT and tuple(c["tile"]) == (0, 1, 0)]
-    steps = [c for c in cands if c["kernel"] != T.TLS_KERNEL_PERSISTENT]
     V = dims[0] * dims[1] * dims[2] * dims[3]
-    return {"workload": "16^3x32 24 corner-wall sources N=80", "best": best,
-            "ms_per_step": p["ms_iter"] / N, "vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3),
-            "onchip_ms_per_step": min((c["ms_per_step"] for c in onchip), default=None),
-            "best_step_kernel_ms_per_step": min((c["ms_per_step"] for c in steps), default=None),
-            "effective_gbs": V * (216 + 48 * nvec) / (p["ms_iter"] / N / 1e3) / 1e9}
+    best, _ = ctx.autotune(gid, nvec, T.TLS_F32, T.TLS_ALL_T, steps=N)
+    runs = {}
+    for name, kern, vb, thr, tile in (("autotuned", T.TLS_KERNEL_AUTO, 0, 0, None),
+                                      ("persistent_onchip", T.TLS_KERNEL_PERSISTENT, 4, 1024, (0, 1, 0)),
+                                      ("persistent_l2", T.TLS_KERNEL_PERSISTENT, 4, 256, (48, 0, 0))):
+        if tile is not None:
+            ctx.tune_set(gid, nvec, T.TLS_F32, T.TLS_ALL_T, kern, vb, thr, tile)
+        x = x0.clone()
+        ctx.smear(gid, x, T.TLS_F32, nvec, N, sigma, storage=T.TLS_F32, kernel=T.TLS_KERNEL_AUTO, stream=stream)
+        p = ctx.get_profile()
+        ms = p["ms_iter"] / N
+        runs[name] = {"ms_per_step": ms, "vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3),
+                      "effective_gbs": V * (216 + 48 * nvec) / (ms / 1e3) / 1e9}
+        if tile is None:
+            runs[name]["kernel"] = best
+    ctx.free_gauge(gid)
+    return {"workload": "16^3x32 24 corner-wall sources N=80", **runs}
 
 
 def our_arm(args):
@@ -454,7 +591,7 @@ def our_arm(args):
     torch.cuda.set_device(local)
     from paper_2301_05518_gb300 import tls
     T = tls
-    w = workload(args.small, args.lattice)
+    w = workload(args.small, args.lattice, args.nvec)
     dims = w["dims"]
     Lx, Ly, Lz, Lt = dims
     V = Lx * Ly * Lz * Lt
@@ -593,24 +730,60 @@ def our_arm(args):
             gbs = p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9
             single[kname] = {"gbs": gbs, "frac": gbs / hbm_peak, "ms_per_step": p["ms_iter"] / 20}
         extra["single_rhs_f32_N20"] = single
+        # the 70% gate (FP32, W f32-18, one vector, planar kernel) as a top-level key
+        result["single_rhs_gate"] = dict(single["single"], kernel="k_step", lattice="64^3x96",
+                                         note="FP32 storage, W f32-18, 1 vector, 20 steps")
+        # accuracy of the headline result: fresh corner walls smeared once (tuned kernel),
+        # vectors 0-2 (corner 0, colours 0-2) on slice 0 against the FP64 oracle
+        from paper_2301_05518_gb300 import synth as _synth
+        fresh = _synth.corner_wall_sources(dims, t=0, dtype=torch.complex64, device="cuda")[:nvec]
+        U0 = U[0:1].cpu().numpy()
+        src0 = fresh[0:3, 0:1].cpu().numpy()
+        accuracy = {}
+        xa = fresh.clone()
+        ctx.smear(gid, xa, T.TLS_F32, nvec, N, sigma, storage=storage, kernel=kernel, stream=stream)
+        accuracy["headline"] = {"max_rel_l2": oracle_rel_err(U0, src0, xa[0:3, 0:1].cpu().numpy(), N, sigma),
+                                "tolerance": 2e-6 * N if storage == T.TLS_F32 else 5e-3,
+                                "sample": "vectors 0-2 on slice 0 (the other slices are zero)"}
+        del xa
         # the same 24-vector workload with 16-bit storage (per-site scale, FP32 arithmetic)
-        if storage != T.TLS_F16:
-            best16, _ = ctx.autotune(gid, nvec, T.TLS_F16, T.TLS_ALL_T, steps=4)
-            x16 = vecs.clone()
-            ctx.smear(gid, x16, T.TLS_F32, nvec, N, sigma, storage=T.TLS_F16, stream=stream)
+        for name16, st16 in (("f16_storage", T.TLS_F16), ("bf16_storage", T.TLS_BF16)):
+            if storage == st16:
+                continue
+            best16, _ = ctx.autotune(gid, nvec, st16, T.TLS_ALL_T, steps=4)
+            x16 = fresh.clone()
+            ctx.smear(gid, x16, T.TLS_F32, nvec, N, sigma, storage=st16, stream=stream)
             p = ctx.get_profile()
-            extra["f16_storage"] = {"vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3),
-                                    "ms_per_step": p["ms_iter"] / N, "kernel": best16,
-                                    "gbs": p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9}
+            extra[name16] = {"vectors_per_s_smear_only": nvec / (p["ms_total"] / 1e3),
+                             "ms_per_step": p["ms_iter"] / N, "kernel": best16,
+                             "gbs": p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9,
+                             "frac": p["iter_bytes"] / (p["ms_iter"] / 1e3) / 1e9 / hbm_peak}
+            accuracy[name16] = {"max_rel_l2": oracle_rel_err(U0, src0, x16[0:3, 0:1].cpu().numpy(), N, sigma),
+                                "tolerance": 5e-3}
             del x16
+        del fresh
         ctx.free_gauge(gid)
+        result["accuracy"] = accuracy
+        # measured arithmetic peaks of this GPU, and the FP64 two-link build against them
+        peaks = {k: T.tls_peak_flops(local, kk) for k, kk in (("fp64_tflops", T.TLS_PEAK_F64),
+                                                                ("fp32_tflops", T.TLS_PEAK_F32),
+                                                                ("fp32x2_tflops", T.TLS_PEAK_F32X2))}
+        extra["arith_peaks"] = peaks
+        build_flops = 3 * 27 * 8 * V  # 3 directions x 27 complex multiply-adds (8 flops) per site
+        result["build"] = {"ms": prof_last["ms_build"], "flops": build_flops,
+                           "tflops": build_flops / (prof_last["ms_build"] / 1e3) / 1e12,
+                           "frac_of_fp64_peak": build_flops / (prof_last["ms_build"] / 1e3) / 1e12 / peaks["fp64_tflops"],
+                           "peak_source": "measured (tls_peak_flops, FP64 FMA chains)"}
         # APE smearing of the links (FP64, staples + projection onto SU(3)), one step
         gid = ctx.load_gauge(U, 4, dims, stream=stream)
         ctx.ape_smear(gid, 0.5, 1, stream=stream)
         p = ctx.get_profile()
         ctx.free_gauge(gid)
         extra["ape_smear"] = {"ms_per_step": p["ms_total"], "alpha": 0.5,
-                              "site_links_per_s": 3 * V / (p["ms_total"] / 1e3)}
+                              "site_links_per_s": 3 * V / (p["ms_total"] / 1e3),
+                              "fp64_tflops_lower_bound": 3 * V * APE_FLOPS_PER_LINK / (p["ms_total"] / 1e3) / 1e12,
+                              "note": "flops counted for the staples, the mix and 3 Newton steps of the polar "
+                                      "projection (a lower bound: the kernel takes up to 8)"}
         if rank == 0 and ws >= 1:
             # CPU baseline: the oracle on a bounded sample, on this machine's host cores
             Lx, Ly, Lz, Lt = dims
@@ -624,13 +797,15 @@ def our_arm(args):
     if not args.no_extra:
         del U, vecs
         torch.cuda.empty_cache()
+        extra["configs_small"] = config01_run(T, ctx, stream)
+        torch.cuda.empty_cache()
         extra["sink_smear"] = sink_run(T, ctx, local, stream, hbm_peak)
         torch.cuda.empty_cache()
         extra["small_lattice"] = small_lattice_run(T, ctx, local, stream, hbm_peak)
         torch.cuda.empty_cache()
         extra["large_mrhs"] = large_mrhs_run(T, ctx, local, stream, hbm_peak)
         torch.cuda.empty_cache()
-        extra["serving"] = serving_run(T, local, n_closed=24, n_open=args.serve_jobs, time_cap_s=25.0,
+        extra["serving"] = serving_run(T, local, n_closed=24, n_open=args.serve_jobs, time_cap_s=150.0,
                                        fp64_cap_s=10.0)
         result["serving_p50_ms"] = extra["serving"]["p50_ms"]
         result["serving_p99_ms"] = extra["serving"]["p99_ms"]

@@ -207,10 +207,9 @@ tls_status tls_smear_onelink(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_p
 
 /* ---- smearing without any device allocation --------------------------------
  * The paper has no counterpart to this entry point.  It serves callers that
- * cannot allocate device memory while they run: code in the middle of a
- * CUDA stream capture (cudaMalloc and cudaFree are not allowed there), a
- * latency-critical host thread (cudaFree synchronises the whole device), or a
- * process whose device memory belongs to another allocator.
+ * cannot allocate device memory while they run: a latency-critical host
+ * thread (cudaFree synchronises the whole device), or a process whose device
+ * memory belongs to another allocator.
  * It computes what tls_smear(..., kernel = TLS_KERNEL_PERSISTENT, ...) does,
  * on device vectors only (`vecs` is device memory of the context's device,
  * canonical layout, smeared in place), and calls no cudaMalloc, cudaFree or
@@ -223,7 +222,9 @@ tls_status tls_smear_onelink(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_p
  * stream capture.  Calls share the array: each clears what must start at
  * zero, and calls whose work overlaps on the GPU race on it.  The gauge must
  * already be built (tls_build_twolink allocates W; this call does not).
- * Synchronous on `stream`.  Errors as tls_smear.                            */
+ * Synchronous on `stream`: it waits for the stream and copies the device
+ * error word into host memory before it returns.  Errors as tls_smear; after
+ * TLS_ERR_TIMEOUT or TLS_ERR_DEVICE the vectors are unspecified.           */
 #define TLS_NOALLOC_SCRATCH_BYTES (32u << 20)
 tls_status tls_smear_noalloc(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int nvec, int N,
                              double width, int timeslice, int storage, void *stream);
@@ -342,6 +343,20 @@ tls_status tls_serve_poll(tls_ctx *ctx, uint64_t job_id, int *done);
  * the same id returns TLS_ERR_NOT_FOUND.  Returns the job's own status.     */
 tls_status tls_serve_wait(tls_ctx *ctx, uint64_t job_id, double timeout_s,
                           tls_job_result *result);
+
+/* ---- measurement helper: arithmetic rate of the GPU ------------------------
+ * Not a step of the method (the paper has no counterpart); it measures the
+ * roof that the FP64 kernels (two-link build, APE step) and the FP32 stencil
+ * arithmetic are reported against.  Runs a kernel of independent FMA chains
+ * (no memory traffic) on `device`, on a stream of its own, calibrated to about
+ * 100 ms per launch, and returns in *tflops the best of several CUDA-event
+ * timed launches, counting 2 flops per FMA (per lane for the packed pair
+ * form).  Allocates nothing.  Errors: TLS_ERR_ARG (unknown kind or NULL
+ * tflops), TLS_ERR_CUDA.                                                    */
+#define TLS_PEAK_F64   0  /* fma.rn.f64                                      */
+#define TLS_PEAK_F32   1  /* fma.rn.f32                                      */
+#define TLS_PEAK_F32X2 2  /* fma.rn.f32x2 (two FP32 lanes per instruction)    */
+tls_status tls_peak_flops(int device, int kind, double *tflops);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtls.so")
 
 SOURCES = ["api.cu", "serve.cpp", "tune.cpp", "noalloc.cu", "k_layout.cu", "k_ape.cu", "k_step_f64.cu", "k_step_f32.cu",
-           "k_step_f16.cu", "k_step_bf16.cu"]
+           "k_step_f16.cu", "k_step_bf16.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

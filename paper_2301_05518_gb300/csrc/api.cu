@@ -261,6 +261,16 @@ tls_status tls_create(tls_ctx **out, int device, uint64_t hbm_cap_bytes)
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) return cuda_fail(e, "tls_create: cudaEventCreate");
     }
+    e = cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&ctx->e_in[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->e_done[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->e_out[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->e_sync[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->e_sync[1], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "tls_create: copy streams and events");
     *out = ctx.release();
     return ok();
 }
@@ -285,6 +295,14 @@ void tls_destroy(tls_ctx *ctx)
         if (ctx->h_err) cudaFreeHost(ctx->h_err);
         for (auto &ev : ctx->ev)
             if (ev) cudaEventDestroy(ev);
+        for (cudaEvent_t ev : ctx->evp) cudaEventDestroy(ev);
+        for (int k = 0; k < 3; ++k)
+            for (cudaEvent_t ev : {ctx->e_in[k], ctx->e_done[k], ctx->e_out[k]})
+                if (ev) cudaEventDestroy(ev);
+        for (cudaEvent_t ev : ctx->e_sync)
+            if (ev) cudaEventDestroy(ev);
+        if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
+        if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
     }
     delete ctx;
 }
@@ -342,31 +360,47 @@ tls_status tls_load_gauge(tls_ctx *ctx, const double *U, int nd, const int dims[
     if (s != TLS_OK) return s;
     cudaError_t e = cudaMemsetAsync(gg.Up, 0, gg.Up_bytes, st);
     const int64_t Vslice = (int64_t)dims[0] * dims[1] * dims[2];
-    const size_t slice_bytes = (size_t)Vslice * nd * 144;
     const void *U_dev = on_device ? (const void *)U : nullptr;
     if (e == cudaSuccess && U_dev) {
         e = launch_ingest_gauge((const double *)U_dev, nd, gg.Up, gg.g, gg.L, st);
     } else if (e == cudaSuccess) {
-        // Host input: stage a few slices at a time.
-        int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(dims[3], (int64_t)(1ULL << 30) / (int64_t)slice_bytes));
+        // Host input: only the spatial links travel (a 2-D copy of the first
+        // 3 of the nd link groups of every site), in slice groups through two
+        // staging slots: the copy of group k+1 (stream s_in) overlaps the
+        // ingest of group k on the launch stream.
+        const size_t site_b = (size_t)nd * 144, spat_b = 3 * 144;
+        const size_t slice_sb = (size_t)Vslice * spat_b;  // staged bytes per slice
+        const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(dims[3], (int64_t)(256ULL << 20) / (int64_t)slice_sb));
+        const int nslot = dims[3] > chunk ? 2 : 1;
         void *tmp = nullptr;
-        s = dev_alloc(ctx, &tmp, slice_bytes * chunk, "tls_load_gauge: staging");
+        s = dev_alloc(ctx, &tmp, slice_sb * chunk * nslot, "tls_load_gauge: staging");
         if (s != TLS_OK) {
             dev_free(ctx, gg.Up, gg.Up_bytes);
             return s;
         }
-        for (int t0 = 0; t0 < dims[3] && e == cudaSuccess; t0 += chunk) {
+        e = cudaEventRecord(ctx->e_sync[0], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_in, ctx->e_sync[0], 0);
+        for (int k = 0, t0 = 0; t0 < dims[3] && e == cudaSuccess; ++k, t0 += chunk) {
             const int nsl = std::min(chunk, dims[3] - t0);
-            e = cudaMemcpyAsync(tmp, (const char *)U + (size_t)t0 * slice_bytes, slice_bytes * nsl,
-                                cudaMemcpyHostToDevice, st);
-            if (e != cudaSuccess) break;
+            const int slot = k % nslot;
+            char *buf = (char *)tmp + (size_t)slot * slice_sb * chunk;
+            if (k >= nslot) e = cudaStreamWaitEvent(ctx->s_in, ctx->e_done[slot], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(buf, spat_b, (const char *)U + (size_t)t0 * Vslice * site_b, site_b, spat_b,
+                                      (size_t)Vslice * nsl, cudaMemcpyHostToDevice, ctx->s_in);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->e_in[slot], ctx->s_in);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->e_in[slot], 0);
             int Lc[4] = {dims[0], dims[1], dims[2], nsl};
-            e = launch_ingest_gauge((const double *)tmp, nd, gg.Up + (size_t)t0 * 8 * 3 * 9 * gg.g.Ps * 2, gg.g, Lc,
-                                    st);
+            if (e == cudaSuccess)
+                e = launch_ingest_gauge((const double *)buf, 3, gg.Up + (size_t)t0 * 8 * 3 * 9 * gg.g.Ps * 2, gg.g, Lc,
+                                        st);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->e_done[slot], st);
         }
         cudaError_t e2 = cudaStreamSynchronize(st);
         if (e == cudaSuccess) e = e2;
-        dev_free(ctx, tmp, slice_bytes * chunk);
+        e2 = cudaStreamSynchronize(ctx->s_in);
+        if (e == cudaSuccess) e = e2;
+        dev_free(ctx, tmp, slice_sb * chunk * nslot);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -599,6 +633,9 @@ tls_status tls_smear(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int
 
 namespace tls {
 
+// Bytes of caller vectors per slice group when they come from host memory.
+constexpr size_t kGroupBytes = size_t(2) << 30;
+
 tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, int vecs_on_device, int nvec, int N,
                       double width, int timeslice, int storage, int kernel, int force_vb, int force_threads,
                       const int *force_tile, void *stream, double *norms_out, int op)
@@ -672,20 +709,26 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         kern = TLS_KERNEL_MRHS;
         for (int k = 0; k < 3; ++k) tile[k] = 0;
     }
-    const int G0 = std::min(nvec, 256);
+    // FP32 and 16-bit records of the interleaved layout come in vector pairs:
+    // a group of an odd number of vectors carries one padding record
+    // (computed, never unpacked).
+    const bool pad_pairs = storage != TLS_F64;
+    auto rec_of = [&](int n) { return pad_pairs ? (n + 1) & ~1 : n; };
+    const int G0 = rec_of(std::min(nvec, 256));
     if (kern == TLS_KERNEL_SINGLE) {
         vb = 1;
         if (threads <= 0) threads = 128;
     } else if (kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS || kern == TLS_KERNEL_MRHS_ZM) {
         // eight vectors per thread: FP32 storage, packed kernel (tile[1] = 2) only
-        const bool vb8 = vb == 8 && storage == TLS_F32 && tile[1] == 2 && kern == TLS_KERNEL_MRHS;
+        const bool vb8 = vb == 8 && storage == TLS_F32 && (tile[1] == 2 || tile[1] == 6 || tile[1] == 7) &&
+                         kern == TLS_KERNEL_MRHS;
         if (vb <= 0 || (vb > 4 && !vb8) || G0 % vb != 0 || (storage == TLS_F64 && vb > 2))
             vb = default_il_vb(storage, G0);
         if (threads == 0) threads = 256;  // < 0: the register-capped variant
         // TMA row staging needs 16-byte copies and a row that fits in shared memory
         if (kern == TLS_KERNEL_MRHS_ROWS &&
             !(rows_applicable(fmt, storage, gg->g, G0, vb, ctx->max_smem) &&
-              rows_applicable(fmt, storage, gg->g, nvec % G0 ? nvec % G0 : G0, vb, ctx->max_smem)))
+              rows_applicable(fmt, storage, gg->g, rec_of(nvec % 256 ? nvec % 256 : 256), vb, ctx->max_smem)))
             kern = TLS_KERNEL_MRHS;
     } else {
         if (vb <= 0) vb = default_vb(storage, nvec);
@@ -704,24 +747,40 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     const bool staged = vecs_dev == nullptr;
 
     // Workspace.
-    size_t a_bytes = (size_t)vs * G;
+    size_t a_bytes = (size_t)vs * (il_layout ? rec_of(G) : G);
     s = ensure(ctx, ctx->A, a_bytes, "tls_smear: vector buffer A");
     if (s == TLS_OK) s = ensure(ctx, ctx->B, a_bytes, "tls_smear: vector buffer B");
-    // alpha per vector in FP64, then the same rounded to FP32 (read by the FP32-arithmetic kernels)
-    const size_t alpha_bytes = sizeof(double) * nvec + sizeof(float) * nvec;
+    // alpha per vector in FP64, then the same rounded to FP32 (read by the FP32-arithmetic
+    // kernels); one more entry of each for a padding record
+    const int nalpha = nvec + 1;
+    const size_t alpha_bytes = sizeof(double) * nalpha + sizeof(float) * nalpha;
     if (s == TLS_OK) s = ensure(ctx, ctx->alpha, alpha_bytes, "tls_smear: alpha");
     if (s == TLS_OK && norms_out)
-        s = ensure(ctx, ctx->partials, sizeof(double) * kNormParts * nvec, "tls_smear: partials");
+        s = ensure(ctx, ctx->partials, sizeof(double) * kNormPartsPerSlice * nsl * nvec, "tls_smear: partials");
     if (s == TLS_OK && norms_out) s = ensure(ctx, ctx->norms, sizeof(double) * nvec, "tls_smear: norms");
-    if (s == TLS_OK && staged)
-        s = ensure(ctx, ctx->staging, io_slice_bytes * nsl * nvec, "tls_smear: host staging");
+    // Host vectors go through slice groups of about kGroupBytes in up to three
+    // rotating staging slots, so that copies in and out overlap the smearing
+    // of other groups.  The persistent kernel takes all slices in one group.
+    int tg = nsl, ngroup = 1, nslot = 1;
+    size_t slot_bytes = 0;
+    if (staged) {
+        const size_t total = io_slice_bytes * nsl * nvec;
+        if (kern != TLS_KERNEL_PERSISTENT && nsl >= 2) {
+            const int64_t want = std::max<int64_t>(4, (int64_t)((total + kGroupBytes - 1) / kGroupBytes));
+            tg = (int)((nsl + std::min<int64_t>(nsl, want) - 1) / std::min<int64_t>(nsl, want));
+            ngroup = (nsl + tg - 1) / tg;
+        }
+        nslot = std::min(ngroup, 3);
+        slot_bytes = (io_slice_bytes * tg * nvec + 255) / 256 * 256;
+        if (s == TLS_OK) s = ensure(ctx, ctx->staging, slot_bytes * nslot, "tls_smear: host staging");
+    }
     if (s != TLS_OK) return s;
-    if (ctx->h_alpha_n < (size_t)nvec) {
+    if (ctx->h_alpha_n < (size_t)nalpha) {
         if (ctx->h_alpha) cudaFreeHost(ctx->h_alpha);
         ctx->h_alpha = nullptr;
         cudaError_t e = cudaMallocHost(&ctx->h_alpha, alpha_bytes);
         if (e != cudaSuccess) return cuda_fail(e, "tls_smear: pinned alpha");
-        ctx->h_alpha_n = nvec;
+        ctx->h_alpha_n = nalpha;
     }
     if (ctx->h_norms_n < (size_t)nvec) {
         if (ctx->h_norms) cudaFreeHost(ctx->h_norms);
@@ -764,178 +823,228 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
     }
 
     const double a = N > 0 ? (op == 0 ? width / (4.0 * N) : width) : 0.0;
-    for (int v = 0; v < nvec; ++v) ctx->h_alpha[v] = a;
-    float *h_alphaf = reinterpret_cast<float *>(ctx->h_alpha + nvec);
-    for (int v = 0; v < nvec; ++v) h_alphaf[v] = (float)a;  // round to nearest, as the kernels' conversion
+    for (int v = 0; v < nalpha; ++v) ctx->h_alpha[v] = a;
+    float *h_alphaf = reinterpret_cast<float *>(ctx->h_alpha + nalpha);
+    for (int v = 0; v < nalpha; ++v) h_alphaf[v] = (float)a;  // round to nearest, as the kernels' conversion
 
     cudaError_t e = cudaSuccess;
     int64_t launches = 0, iter_launches = 0;
     const bool prof = ctx->profiling;
-    float t_pack = 0, t_iter = 0, t_unpack = 0, t_h2d = 0;
-    // Phase timing: events on the launch stream, accumulated per vector group.
-    auto mark = [&](int k) {
-        if (prof) cudaEventRecord(ctx->ev[k], st);
+    // Profiling: (begin, end) event pairs per phase, read after the final synchronisation.
+    enum { PH_H2D, PH_PACK, PH_ITER, PH_UNPACK, PH_D2H, PH_N };
+    struct Span {
+        int a, b, phase;
     };
-    auto lap = [&](int a0, int a1) -> float {
-        float ms = 0.f;
-        if (prof) {
-            cudaEventSynchronize(ctx->ev[a1]);
-            cudaEventElapsedTime(&ms, ctx->ev[a0], ctx->ev[a1]);
+    std::vector<Span> spans;
+    int nev = 0;
+    auto ev_rec = [&](cudaStream_t s) -> int {
+        if (!prof) return -1;
+        if (nev >= (int)ctx->evp.size()) {
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreate(&ev) != cudaSuccess) return -1;
+            ctx->evp.push_back(ev);
         }
-        return ms;
+        cudaEventRecord(ctx->evp[nev], s);
+        return nev++;
     };
-    mark(0);
+    auto span = [&](int a0, int a1, int phase) {
+        if (a0 >= 0 && a1 >= 0) spans.push_back(Span{a0, a1, phase});
+    };
+    const int ev_begin = ev_rec(st);
     e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->alpha.p, ctx->h_alpha, alpha_bytes, cudaMemcpyHostToDevice, st);
 
-    // Caller buffer (device) or staging copy of the selected slices.
-    const char *src_io = nullptr;
-    char *dst_io = nullptr;
-    int64_t io_vstride_sites = V;  // sites between vectors in the canonical buffer
-    int t_rel = t_first;
-    if (!staged) {
-        src_io = (const char *)vecs_dev;
-        dst_io = (char *)vecs_dev;
-    } else {
-        const size_t width_b = io_slice_bytes * nsl;
-        const size_t pitch = (size_t)V * 6 * io_elem;
-        if (e == cudaSuccess)
-            e = cudaMemcpy2DAsync(ctx->staging.p, width_b, (const char *)vecs + (size_t)t_first * io_slice_bytes, pitch,
-                                  width_b, nvec, cudaMemcpyHostToDevice, st);
-        src_io = (const char *)ctx->staging.p;
-        dst_io = (char *)ctx->staging.p;
-        io_vstride_sites = Vslice * nsl;
-        t_rel = 0;
-    }
-    mark(1);
-    if (prof) t_h2d = lap(0, 1);
-
-    const char *W0 = field + (size_t)t_first * 8 * 3 * g.Ps * wfmt_bytes(fmt);
-    const size_t io_vec_bytes = (size_t)io_vstride_sites * 6 * io_elem;
-    for (int g0 = 0; g0 < nvec && e == cudaSuccess; g0 += G) {
-        const int gn = std::min(G, nvec - g0);
-        const char *src_g = src_io + (size_t)g0 * io_vec_bytes;
-        char *dst_g = dst_io + (size_t)g0 * io_vec_bytes;
-        const bool il = il_layout;
-        mark(2);
-        e = il ? launch_pack_il(src_g, io_prec, io_vstride_sites, (char *)ctx->A.p, storage, g, gg->L, t_rel, nsl, gn,
-                                    gn, 0, st)
-               : launch_pack_vectors(src_g, io_prec, io_vstride_sites, (char *)ctx->A.p, storage, vs, g, gg->L, t_rel,
-                                     nsl, gn, st);
-        ++launches;
-        mark(3);
-        char *result = (char *)ctx->A.p;
-        const double *alpha_g = (const double *)ctx->alpha.p + g0;
-        const float *alphaf_g = reinterpret_cast<const float *>((const double *)ctx->alpha.p + nvec) + g0;
-        if (N > 0 && e == cudaSuccess) {
-            if (kern == TLS_KERNEL_PERSISTENT) {
-                pa.W = W0;
-                pa.in = (const char *)ctx->A.p;
-                pa.out = (char *)ctx->B.p;
-                pa.scr[0] = (char *)ctx->S0.p;
-                pa.scr[1] = (char *)ctx->S1.p;
-                pa.alpha = alpha_g;
-                pa.g = g;
-                pa.nblk = nblk;
-                pa.nvec = gn;
-                pa.N = N;
-                pa.vstride = vs;
-                pa.wfmt = fmt;
-                pa.prec = storage;
-                pa.vb = vb;
-                pa.threads = threads;
-                pa.bar = ctx->d_bar;
-                pa.err = ctx->d_err;
-                pa.budget = ctx->barrier_budget > 0 ? ctx->barrier_budget : kDefaultBudget;
-                pa.stream = st;
-                e = cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), st);
-                if (e == cudaSuccess) e = launch_persistent(pa);
-                ++launches;
-                ++iter_launches;
-                result = (char *)ctx->B.p;
-            } else {
-                StepArgs sa{};
-                sa.W = W0;
-                sa.g = g;
-                sa.nblk = nblk;
-                sa.wfmt = fmt;
-                sa.prec_in = sa.prec_out = storage;
-                sa.vb = vb;
-                sa.threads = threads;
-                sa.stream = st;
-                sa.vstride_in = sa.vstride_out = vs;
-                for (int k = 0; k < 3; ++k) sa.tile[k] = tile[k];
-                const int sub_groups = kern == TLS_KERNEL_SINGLE ? gn : 1;
-                sa.nvec = kern == TLS_KERNEL_SINGLE ? 1 : gn;
-                for (int gi = 0; gi < sub_groups && e == cudaSuccess; ++gi) {
-                    char *x = (char *)ctx->A.p + (size_t)gi * vs;
-                    char *y = (char *)ctx->B.p + (size_t)gi * vs;
-                    for (int it = 0; it < N && e == cudaSuccess; ++it) {
-                        sa.in = (it & 1) ? y : x;
-                        sa.out = (it & 1) ? x : y;
-                        sa.alpha = alpha_g + gi;
-                        sa.alphaf = alphaf_g + gi;
-                        e = op == 1                     ? launch_hop(sa)
-                            : kern == TLS_KERNEL_MRHS_ROWS ? launch_step_rows(sa, ctx->d_err)
-                            : kern == TLS_KERNEL_MRHS_ZM ? launch_step_zm(sa)
-                            : il                         ? launch_step_il(sa)
-                                                         : launch_step(sa);
-                        ++launches;
-                        ++iter_launches;
-                    }
-                }
-                result = (N & 1) ? (char *)ctx->B.p : (char *)ctx->A.p;
-            }
-        }
-        mark(4);
-        if (e == cudaSuccess) {
-            e = il ? launch_unpack_il(result, storage, dst_g, io_prec, io_vstride_sites, g, gg->L, t_rel, nsl, gn, gn, 0,
-                                      st)
-                   : launch_unpack_vectors(result, storage, vs, dst_g, io_prec, io_vstride_sites, g, gg->L, t_rel, nsl,
-                                           gn, nullptr, nullptr, st);
+    // One pass of the method over slices [t_abs, t_abs + ns): their canonical
+    // vectors are at src / dst (vector stride vsites sites; slice t_abs is
+    // relative slice t_rel0 there).  Packs, runs the N steps, unpacks, and
+    // writes the norm partials of these slices at their place in the
+    // per-slice partials of the call (so any split into slice groups gives
+    // the same norms).
+    const size_t io_elem_b = io_elem;
+    auto run_slices = [&](const char *src_io, char *dst_io, int64_t vsites, int t_rel0, int t_abs, int ns) {
+        const int nb = ns * 8;
+        const int64_t vsg = (int64_t)nb * g.Ps * VBY;  // packed bytes per vector of these slices
+        const char *Wg = field + (size_t)t_abs * 8 * 3 * g.Ps * wfmt_bytes(fmt);
+        const size_t io_vec_bytes = (size_t)vsites * 6 * io_elem_b;
+        for (int g0 = 0; g0 < nvec && e == cudaSuccess; g0 += G) {
+            const int gn = std::min(G, nvec - g0);
+            const int rn = il_layout ? rec_of(gn) : gn;  // records per site in the packed buffers
+            const char *src_g = src_io + (size_t)g0 * io_vec_bytes;
+            char *dst_g = dst_io + (size_t)g0 * io_vec_bytes;
+            const bool il = il_layout;
+            const int m0 = ev_rec(st);
+            e = il ? launch_pack_il(src_g, io_prec, vsites, (char *)ctx->A.p, storage, g, gg->L, t_rel0, ns, gn, rn, 0,
+                                    st)
+                   : launch_pack_vectors(src_g, io_prec, vsites, (char *)ctx->A.p, storage, vsg, g, gg->L, t_rel0, ns,
+                                         gn, st);
             ++launches;
+            const int m1 = ev_rec(st);
+            char *result = (char *)ctx->A.p;
+            const double *alpha_g = (const double *)ctx->alpha.p + g0;
+            const float *alphaf_g = reinterpret_cast<const float *>((const double *)ctx->alpha.p + nalpha) + g0;
+            if (N > 0 && e == cudaSuccess) {
+                if (kern == TLS_KERNEL_PERSISTENT) {
+                    pa.W = Wg;
+                    pa.in = (const char *)ctx->A.p;
+                    pa.out = (char *)ctx->B.p;
+                    pa.scr[0] = (char *)ctx->S0.p;
+                    pa.scr[1] = (char *)ctx->S1.p;
+                    pa.alpha = alpha_g;
+                    pa.g = g;
+                    pa.nblk = nb;
+                    pa.nvec = gn;
+                    pa.N = N;
+                    pa.vstride = vsg;
+                    pa.wfmt = fmt;
+                    pa.prec = storage;
+                    pa.vb = vb;
+                    pa.threads = threads;
+                    pa.bar = ctx->d_bar;
+                    pa.err = ctx->d_err;
+                    pa.budget = ctx->barrier_budget > 0 ? ctx->barrier_budget : kDefaultBudget;
+                    pa.stream = st;
+                    e = cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), st);
+                    if (e == cudaSuccess) e = launch_persistent(pa);
+                    ++launches;
+                    ++iter_launches;
+                    result = (char *)ctx->B.p;
+                } else {
+                    StepArgs sa{};
+                    sa.W = Wg;
+                    sa.g = g;
+                    sa.nblk = nb;
+                    sa.wfmt = fmt;
+                    sa.prec_in = sa.prec_out = storage;
+                    sa.vb = vb;
+                    sa.threads = threads;
+                    sa.stream = st;
+                    sa.err = ctx->d_err;
+                    sa.vstride_in = sa.vstride_out = vsg;
+                    for (int k = 0; k < 3; ++k) sa.tile[k] = tile[k];
+                    const int sub_groups = kern == TLS_KERNEL_SINGLE ? gn : 1;
+                    sa.nvec = kern == TLS_KERNEL_SINGLE ? 1 : rn;
+                    for (int gi = 0; gi < sub_groups && e == cudaSuccess; ++gi) {
+                        char *x = (char *)ctx->A.p + (size_t)gi * vsg;
+                        char *y = (char *)ctx->B.p + (size_t)gi * vsg;
+                        for (int it = 0; it < N && e == cudaSuccess; ++it) {
+                            sa.in = (it & 1) ? y : x;
+                            sa.out = (it & 1) ? x : y;
+                            sa.alpha = alpha_g + gi;
+                            sa.alphaf = alphaf_g + gi;
+                            e = op == 1                         ? launch_hop(sa)
+                                : kern == TLS_KERNEL_MRHS_ROWS  ? launch_step_rows(sa, ctx->d_err)
+                                : kern == TLS_KERNEL_MRHS_ZM    ? launch_step_zm(sa)
+                                : il                            ? launch_step_il(sa)
+                                                                : launch_step(sa);
+                            ++launches;
+                            ++iter_launches;
+                        }
+                    }
+                    result = (N & 1) ? (char *)ctx->B.p : (char *)ctx->A.p;
+                }
+            }
+            const int m2 = ev_rec(st);
+            if (e == cudaSuccess) {
+                e = il ? launch_unpack_il(result, storage, dst_g, io_prec, vsites, g, gg->L, t_rel0, ns, gn, rn, 0, st)
+                       : launch_unpack_vectors(result, storage, vsg, dst_g, io_prec, vsites, g, gg->L, t_rel0, ns, gn,
+                                               nullptr, nullptr, st);
+                ++launches;
+            }
+            const int m3 = ev_rec(st);
+            span(m0, m1, PH_PACK);
+            span(m1, m2, PH_ITER);
+            span(m2, m3, PH_UNPACK);
         }
-        mark(5);
-        if (prof) {
-            t_pack += lap(2, 3);
-            t_iter += lap(3, 4);
-            t_unpack += lap(4, 5);
+        if (e == cudaSuccess && norms_out) {
+            const int m0 = ev_rec(st);
+            e = launch_norm_partials(dst_io + (size_t)t_rel0 * io_slice_bytes, io_prec, vsites, Vslice, ns, nvec,
+                                     (double *)ctx->partials.p, (int64_t)nsl * kNormPartsPerSlice,
+                                     (int64_t)(t_abs - t_first) * kNormPartsPerSlice, st);
+            ++launches;
+            span(m0, ev_rec(st), PH_UNPACK);
         }
+    };
+
+    if (!staged) {
+        run_slices((const char *)vecs_dev, (char *)vecs_dev, V, t_first, t_first, nsl);
+    } else {
+        // Host vectors: slice groups through rotating staging slots.  Group k
+        // is copied in on s_in while group k-1 is smeared on the launch stream
+        // and group k-2 is copied out on s_out; each slot is refilled only after
+        // its previous group has left (events).  One 2-D copy per group and
+        // direction (all vectors, the group's slices).
+        const char *hsrc = (const char *)vecs;
+        const size_t pitch = (size_t)V * 6 * io_elem;
+        auto group_slices = [&](int k) { return std::min(tg, nsl - k * tg); };
+        e = e == cudaSuccess ? cudaEventRecord(ctx->e_sync[0], st) : e;
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_in, ctx->e_sync[0], 0);
+        auto h2d = [&](int k) {
+            const int slot = k % nslot;
+            const int ns = group_slices(k);
+            const size_t width_b = io_slice_bytes * ns;
+            if (k >= nslot && e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_in, ctx->e_out[slot], 0);
+            const int c0 = ev_rec(ctx->s_in);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync((char *)ctx->staging.p + slot * slot_bytes, width_b,
+                                      hsrc + (size_t)(t_first + k * tg) * io_slice_bytes, pitch, width_b, nvec,
+                                      cudaMemcpyHostToDevice, ctx->s_in);
+            span(c0, ev_rec(ctx->s_in), PH_H2D);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->e_in[slot], ctx->s_in);
+        };
+        h2d(0);
+        if (ngroup > 1) h2d(1);
+        for (int k = 0; k < ngroup && e == cudaSuccess; ++k) {
+            const int slot = k % nslot;
+            const int ns = group_slices(k);
+            char *buf = (char *)ctx->staging.p + slot * slot_bytes;
+            e = cudaStreamWaitEvent(st, ctx->e_in[slot], 0);
+            if (e == cudaSuccess) run_slices(buf, buf, Vslice * ns, 0, t_first + k * tg, ns);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->e_done[slot], st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ctx->e_done[slot], 0);
+            const size_t width_b = io_slice_bytes * ns;
+            const int c0 = ev_rec(ctx->s_out);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync((char *)vecs + (size_t)(t_first + k * tg) * io_slice_bytes, pitch, buf, width_b,
+                                      width_b, nvec, cudaMemcpyDeviceToHost, ctx->s_out);
+            span(c0, ev_rec(ctx->s_out), PH_D2H);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->e_out[slot], ctx->s_out);
+            if (k + 2 < ngroup) h2d(k + 2);
+        }
+        // the launch stream resumes after the last copy out (copies on s_out are in order)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->e_out[(ngroup - 1) % nslot], 0);
     }
     if (e == cudaSuccess && norms_out) {
-        // ||psi_v||^2 over the smeared slices of the canonical result.
-        const char *first = dst_io + (size_t)t_rel * io_slice_bytes;
-        e = launch_norm_partials(first, io_prec, io_vstride_sites, Vslice * nsl, nvec, (double *)ctx->partials.p, st);
-        if (e == cudaSuccess)
-            e = launch_reduce_norms((const double *)ctx->partials.p, kNormParts, nvec, (double *)ctx->norms.p, st);
-        launches += 2;
+        e = launch_reduce_norms((const double *)ctx->partials.p, nsl * kNormPartsPerSlice, nvec,
+                                (double *)ctx->norms.p, st);
+        ++launches;
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ctx->h_norms, ctx->norms.p, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st);
     }
-    mark(6);
-    if (e == cudaSuccess && staged) {
-        const size_t width_b = io_slice_bytes * nsl;
-        const size_t pitch = (size_t)V * 6 * io_elem;
-        e = cudaMemcpy2DAsync((char *)vecs + (size_t)t_first * io_slice_bytes, pitch, ctx->staging.p, width_b,
-                              width_b, nvec, cudaMemcpyDeviceToHost, st);
-    }
-    mark(7);
+    const int ev_end = ev_rec(st);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t es = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = es;
+    if (staged) {  // nothing may still be copying from or to the caller's host buffer
+        es = cudaStreamSynchronize(ctx->s_in);
+        if (e == cudaSuccess) e = es;
+        es = cudaStreamSynchronize(ctx->s_out);
+        if (e == cudaSuccess) e = es;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "tls_smear");
     herr = *ctx->h_err;
     if (prof) {
         tls_profile &p = ctx->prof;
         p = tls_profile{};
-        p.ms_total = elapsed(ctx->ev[0], ctx->ev[7]);
-        p.ms_h2d = t_h2d;
-        p.ms_pack = t_pack;
-        p.ms_iter = t_iter;
-        p.ms_unpack = t_unpack + elapsed(ctx->ev[5], ctx->ev[6]);
-        p.ms_d2h = elapsed(ctx->ev[6], ctx->ev[7]);
+        double ph[PH_N] = {0, 0, 0, 0, 0};
+        for (const Span &sp : spans) ph[sp.phase] += elapsed(ctx->evp[sp.a], ctx->evp[sp.b]);
+        p.ms_total = ev_begin >= 0 && ev_end >= 0 ? elapsed(ctx->evp[ev_begin], ctx->evp[ev_end]) : 0.0;
+        p.ms_h2d = ph[PH_H2D];
+        p.ms_pack = ph[PH_PACK];
+        p.ms_iter = ph[PH_ITER];
+        p.ms_unpack = ph[PH_UNPACK];
+        p.ms_d2h = ph[PH_D2H];
         p.launches = launches;
         p.iter_launches = iter_launches;
         const double sites = (double)nblk * g.Vs;

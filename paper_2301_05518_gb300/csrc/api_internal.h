@@ -117,6 +117,11 @@ struct tls_ctx {
     bool profiling = false;
     tls_profile prof{};
     cudaEvent_t ev[8] = {};
+    std::vector<cudaEvent_t> evp;           // timing events of one smear call (grown on demand)
+
+    // host-buffer pipeline: copies in / out on their own streams, ordered by events
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t e_in[3] = {}, e_done[3] = {}, e_out[3] = {}, e_sync[2] = {};
 
     std::map<tls::TuneKey, tls::TuneVal> tune;
 

@@ -292,18 +292,23 @@ __global__ void k_unpack_il(const char *__restrict__ src, IO *__restrict__ dst, 
     }
 }
 
-// Partial sums of |psi|^2 over `count` sites of each canonical vector:
-// CTA (part, v) takes a fixed strided subset, so the sum order is fixed.
+// Partial sums of |psi|^2 of canonical vectors, per (vector, slice, part):
+// CTA (s * kNormPartsPerSlice + p, v) takes a fixed strided subset of the
+// reals of slice s of vector v, so each partial depends only on its own slice
+// and the sum order is fixed.  Partial (v, s, p) goes to
+// partials[v * part_stride + part_off + s * kNormPartsPerSlice + p].
 template <typename IO>
-__global__ void __launch_bounds__(256) k_norm_partials(const IO *__restrict__ base, int64_t vstride, int64_t count,
-                                                       double *__restrict__ partials)
+__global__ void __launch_bounds__(256) k_norm_partials(const IO *__restrict__ base, int64_t vstride, int64_t slice_sites,
+                                                       double *__restrict__ partials, int64_t part_stride,
+                                                       int64_t part_off)
 {
     __shared__ double red[256];
     const int v = blockIdx.y;
-    const IO *p = base + (int64_t)v * vstride * 6;
-    const int64_t n = count * 6;
+    const int sl = blockIdx.x / kNormPartsPerSlice, part = blockIdx.x - sl * kNormPartsPerSlice;
+    const IO *p = base + ((int64_t)v * vstride + (int64_t)sl * slice_sites) * 6;
+    const int64_t n = slice_sites * 6;
     double acc = 0.0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t k = (int64_t)part * blockDim.x + threadIdx.x; k < n; k += (int64_t)kNormPartsPerSlice * blockDim.x) {
         const double x = (double)p[k];
         acc = fma(x, x, acc);
     }
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(256) k_norm_partials(const IO *__restrict__ ba
         if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) partials[(int64_t)v * gridDim.x + blockIdx.x] = red[0];
+    if (threadIdx.x == 0) partials[(int64_t)v * part_stride + part_off + blockIdx.x] = red[0];
 }
 
 // Copies the interleaved records of one x'-row (hx sites starting at site r of
@@ -666,15 +671,18 @@ cudaError_t launch_unpack_il(const char *src, int prec, void *dst, int io_prec, 
     return cudaErrorNotSupported;
 }
 
-cudaError_t launch_norm_partials(const void *base, int io_prec, int64_t vstride_sites, int64_t count, int nvec,
-                                 double *partials, cudaStream_t s)
+cudaError_t launch_norm_partials(const void *base, int io_prec, int64_t vstride_sites, int64_t slice_sites, int nsl,
+                                 int nvec, double *partials, int64_t part_stride, int64_t part_off, cudaStream_t s)
 {
-    if (nvec == 0) return cudaSuccess;
-    dim3 grid(kNormParts, nvec);
+    if (nvec == 0 || nsl == 0) return cudaSuccess;
+    if ((int64_t)nsl * kNormPartsPerSlice > 0x7fffffff || nvec > 65535) return cudaErrorInvalidValue;
+    dim3 grid(nsl * kNormPartsPerSlice, nvec);
     if (io_prec == P_F64)
-        k_norm_partials<double><<<grid, 256, 0, s>>>((const double *)base, vstride_sites, count, partials);
+        k_norm_partials<double><<<grid, 256, 0, s>>>((const double *)base, vstride_sites, slice_sites, partials,
+                                                      part_stride, part_off);
     else if (io_prec == P_F32)
-        k_norm_partials<float><<<grid, 256, 0, s>>>((const float *)base, vstride_sites, count, partials);
+        k_norm_partials<float><<<grid, 256, 0, s>>>((const float *)base, vstride_sites, slice_sites, partials,
+                                                     part_stride, part_off);
     else
         return cudaErrorNotSupported;
     return cudaGetLastError();

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 
+#include "k_ilt.cuh"
 #include "tls_dev.cuh"
 #include "tls_internal.h"
 
@@ -259,7 +260,6 @@ __device__ __forceinline__ R alpha_of(const double *__restrict__ alpha, const fl
 // Packed FP32 pair forms of mv_add / mdv_add for VB vectors: every (re, im)
 // accumulator gets, lane by lane, the FMA sequence of cmac / cmacc, with the
 // broadcast W pairs built once per element for all VB vectors.
-__device__ __forceinline__ float2 f2swap(float2 a) { return make_float2(a.y, a.x); }
 
 template <int VB>
 __device__ __forceinline__ void mv_add_x2(const cpx<float> m[9], const cpx<float> p[VB][3], float2 acc[VB][3])
@@ -992,6 +992,13 @@ inline int il_spb(int nvec, int threads)
 // ONLYX: only the packed FP32 pair kernel is instantiated (eight vectors per thread).
 template <int VP, int WF, int VB, bool ONLYX = false> cudaError_t step_il_launch(const StepArgs &a)
 {
+    // whole-row CTAs with the W rows staged by TMA bulk copies (k_ilt.cuh); a
+    // shape or format it does not cover runs the packed kernel instead
+    const bool ilt = a.tile[1] == 6 || a.tile[1] == 7;
+    if (ilt) {
+        const cudaError_t e = ilt_launch<VP, WF, VB>(a);
+        if (e != cudaErrorNotSupported) return e;
+    }
     const int tx = a.nvec / VB;
     // a strip of spb consecutive x' per CTA; tile[0] > 0 sets spb explicitly
     // threads = -128 selects the 64-register variant (CTAs of <= 128 threads)
@@ -1002,8 +1009,8 @@ template <int VP, int WF, int VB, bool ONLYX = false> cudaError_t step_il_launch
     spb = std::max(1, std::min(spb, cap / tx));
     spb = std::min(spb, a.g.hx);  // a strip never spans more than one row
     // the packed kernel also serves slot batches (active table); the other staged forms do not
-    const bool packed = (a.tile[1] == 2 || ((a.tile[1] == 3 || a.tile[1] == 5) && a.active == nullptr)) && a.alphaf &&
-                        VP != P_F64;
+    const bool packed = (a.tile[1] == 2 || ilt || ((a.tile[1] == 3 || a.tile[1] == 5) && a.active == nullptr)) &&
+                        a.alphaf && VP != P_F64;
     const bool staged = a.tile[1] > 0 && a.active == nullptr && a.alphaf;
     constexpr int kPackB = 6 * 9 * 16;  // W packs per site of the packed kernel
     // shared memory within the default dynamic limit (48 KB)
@@ -1016,7 +1023,7 @@ template <int VP, int WF, int VB, bool ONLYX = false> cudaError_t step_il_launch
     dim3 grid((a.g.hx + spb - 1) / spb, a.g.hy, (unsigned)a.g.hz * a.nblk);
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
     if constexpr (ONLYX) {
-        if (!packed || a.tile[1] != 2 || a.active) return cudaErrorNotSupported;
+        if (!packed || (a.tile[1] != 2 && !ilt) || a.active) return cudaErrorNotSupported;
         k_step_ilx<VP, WF, VB, false><<<grid, block, kPackB * spb, a.stream>>>(a.W, a.in, a.out, a.alpha, a.alphaf,
                                                                                nullptr, a.g, a.nvec);
         return cudaGetLastError();

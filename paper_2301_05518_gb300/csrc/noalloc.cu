@@ -2,11 +2,11 @@
 // scratch in a fixed, library-owned device array instead of cudaMalloc.
 //
 // Who needs it: code that must not allocate device memory while it runs.
-// Examples are a caller in the middle of a CUDA stream capture, where
-// cudaMalloc/cudaFree are not allowed; a host thread on a latency-critical
-// path, where cudaFree synchronises the whole device; and a process whose
-// device memory is owned by another allocator (a framework's caching pool)
-// that must stay the only one handing out memory.  Such callers still pass
+// Examples are a host thread on a latency-critical path, where cudaFree
+// synchronises the whole device, and a process whose device memory is owned
+// by another allocator (a framework's caching pool) that must stay the only
+// one handing out memory.  The call itself synchronises its stream and reads
+// the error word back into host memory before it returns.  Such callers still pass
 // their vectors in and get them back in place; everything else the call
 // needs (the packed copies of the vectors, the persistent kernel's scratch
 // ping-pong, its barrier words, the per-vector alpha and the error word)
@@ -19,7 +19,9 @@
 // call reuses the same array, which keeps whatever the previous call left:
 // the words that must start at zero (barrier, error) are cleared by each
 // call, and two calls whose work overlaps on the GPU (different streams or
-// host threads without ordering) race on the array.
+// host threads without ordering) race on the array.  When the call returns
+// TLS_ERR_TIMEOUT or TLS_ERR_DEVICE the caller's vectors hold an unspecified
+// mix of input and partial results.
 #include <cmath>
 #include <mutex>
 

@@ -74,6 +74,8 @@ struct Batch {
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool launched = false;
+    int *d_err = nullptr;    // device error word of this batch's kernels (bounded waits)
+    int *h_err = nullptr;    // pinned copy, read after each round
 
     int active_slots() const
     {
@@ -122,20 +124,26 @@ void destroy_batch(tls_ctx *ctx, Batch *b)
     if (b->h_alpha) cudaFreeHost(b->h_alpha);
     if (b->h_active) cudaFreeHost(b->h_active);
     if (b->stream) cudaStreamDestroy(b->stream);
+    dev_free(ctx, b->d_err, 256);
+    if (b->h_err) cudaFreeHost(b->h_err);
 }
+
+// Slots of a batch: FP32 and 16-bit record groups hold an even number of vectors.
+int batch_slots(int storage, int max_slots) { return storage != TLS_F64 ? (max_slots + 1) & ~1 : max_slots; }
 
 size_t batch_bytes(const Gauge &gg, int storage, int timeslice, int S, int K)
 {
+    S = batch_slots(storage, S);
     const int nsl = timeslice < 0 ? gg.L[3] : 1;
     const int64_t vs = (int64_t)nsl * 8 * gg.g.Ps * vfmt_bytes(storage);
-    return 2 * (size_t)vs * S + 2 * (size_t)K * S * 8 + (size_t)K * S * 4;
+    return 2 * (size_t)vs * S + 2 * (size_t)K * S * 8 + (size_t)K * S * 4 + 256;
 }
 
 tls_status make_batch(tls_ctx *ctx, Server *sv, const BatchKey &key, const Gauge &gg, Batch **out)
 {
     std::unique_ptr<Batch> b(new Batch());
     b->key = key;
-    b->S = sv->opts.max_slots;
+    b->S = batch_slots(key.storage, sv->opts.max_slots);
     b->K = sv->opts.steps_per_launch;
     b->vb = default_il_vb(key.storage, b->S);
     b->nsl = key.timeslice < 0 ? gg.L[3] : 1;
@@ -149,6 +157,8 @@ tls_status make_batch(tls_ctx *ctx, Server *sv, const BatchKey &key, const Gauge
     if (s == TLS_OK) s = dev_alloc(ctx, (void **)&b->buf[1], b->buf_bytes, "serve: batch buffer B");
     if (s == TLS_OK) s = dev_alloc(ctx, (void **)&b->d_alpha, b->alpha_bytes, "serve: alpha table");
     if (s == TLS_OK) s = dev_alloc(ctx, (void **)&b->d_active, b->tab_bytes, "serve: active table");
+    if (s == TLS_OK) s = dev_alloc(ctx, (void **)&b->d_err, 256, "serve: error word");
+    if (s == TLS_OK && cudaMallocHost(&b->h_err, sizeof(int)) != cudaSuccess) s = fail(TLS_ERR_NOMEM, "serve: pinned word");
     if (s == TLS_OK && cudaMallocHost(&b->h_alpha, b->alpha_bytes) != cudaSuccess) s = fail(TLS_ERR_NOMEM, "serve: pinned table");
     if (s == TLS_OK && cudaMallocHost(&b->h_active, b->tab_bytes) != cudaSuccess) s = fail(TLS_ERR_NOMEM, "serve: pinned table");
     if (s == TLS_OK && cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -157,6 +167,8 @@ tls_status make_batch(tls_ctx *ctx, Server *sv, const BatchKey &key, const Gauge
         destroy_batch(ctx, b.get());
         return s;
     }
+    cudaMemsetAsync(b->d_err, 0, 256, b->stream);
+    *b->h_err = 0;
     cudaMemsetAsync(b->buf[0], 0, b->buf_bytes, b->stream);
     cudaMemsetAsync(b->buf[1], 0, b->buf_bytes, b->stream);
     b->slot_job.assign(b->S, nullptr);
@@ -314,8 +326,11 @@ cudaError_t launch_round(tls_ctx *ctx, Server *sv, Batch *b)
     sa.prec_in = sa.prec_out = b->key.storage;
     sa.vb = b->vb;
     sa.threads = 128;
-    // the packed FP32 pair kernel (W broadcast pairs in shared memory); FP64 batches use the plain one
-    if (b->key.storage != TLS_F64) sa.tile[1] = 2;
+    // FP32 and 16-bit batches: whole-row CTAs with the W rows staged by TMA and
+    // vector-pair arithmetic (the packed kernel where the row shape does not
+    // allow it); FP64 batches use the plain interleaved kernel
+    if (b->key.storage != TLS_F64) sa.tile[1] = 6;
+    sa.err = b->d_err;
     const float *d_alphaf = reinterpret_cast<const float *>(b->d_alpha + (size_t)b->K * b->S);
     sa.stream = b->stream;
     auto issue = [&]() -> cudaError_t {
@@ -350,6 +365,7 @@ cudaError_t launch_round(tls_ctx *ctx, Server *sv, Batch *b)
     } else {
         e = issue();
     }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e != cudaSuccess) return e;
     for (int s = 0; s < b->S; ++s) {
         if (b->slot_left[s] <= 0) continue;
@@ -463,6 +479,15 @@ void scheduler(tls_ctx *ctx, Server *sv)
             for (size_t k = 0; k < running.size(); ++k) {
                 if (status[k] != cudaSuccess) {
                     fail_batch(ctx, sv, running[k], cuda_fail(status[k], "serve: round"));
+                    continue;
+                }
+                if (*running[k]->h_err) {  // a bounded device wait ran out: the batch's results are void
+                    const int herr = *running[k]->h_err;
+                    *running[k]->h_err = 0;
+                    cudaMemsetAsync(running[k]->d_err, 0, sizeof(int), running[k]->stream);
+                    fail_batch(ctx, sv, running[k],
+                               fail((herr & DERR_TIMEOUT) ? TLS_ERR_TIMEOUT : TLS_ERR_DEVICE,
+                                    "serve: device error word 0x%x", herr));
                     continue;
                 }
                 retire(ctx, sv, running[k]);

@@ -403,18 +403,22 @@ template <> struct VFmt<P_BF16> : VFmtH<__nv_bfloat16> {};
 // Interleaved (vector-innermost) records, per (slice, sublattice) block of
 // Ps sites and nvec vectors:
 //   F64 / F32: three colour planes; plane c holds, for every site i, the nvec
-//              complex numbers (double2 / float2) of colour c contiguously:
-//              element (c, i, v) at ((c * Ps + i) * nvec + v) * 16 / 8 bytes
-//              from the block, so colour c of consecutive sites is contiguous;
-//   16-bit   : one 16-byte record per (site, vector) {3 x half2, float scale}
-//              at (i * nvec + v) * 16 bytes.
+//              complex numbers of colour c contiguously: element (c, i, v) in
+//              the 16 / 8 bytes at ((c * Ps + i) * nvec + v) * 16 / 8 from the
+//              block (F32: the two vectors of a 16-byte word interleave their
+//              real and imaginary parts, see VRec<P_F32>), so colour c of
+//              consecutive sites is contiguous;
+//   16-bit   : 16 bytes per (site, vector), vectors 2u and 2u + 1 of a site
+//              sharing the 32-byte record at (i * nvec + 2u) * 16 bytes (see
+//              VRecH).
 // The block occupies Ps * nvec * vfmt_bytes bytes either way.  A site pointer
 // is block + i * nvec * SB; colour planes are cs = Ps * nvec elements apart.
 // A thread that owns VB vectors of a site reads vector units t, t + T, ...
-// (T = nvec / VB threads per site), a unit being what one 16-byte word holds
-// per colour (two F32 vectors, one otherwise); F32 threads with VB = 4 own the
-// adjacent units 2t, 2t+1 and read them with one 32-byte load.  Consecutive
-// lanes read consecutive words, across site boundaries too.
+// (T = nvec / VB threads per site), a unit being two vectors for F32 and
+// 16-bit storage (one 16-byte word per colour, one 32-byte record), one for
+// F64; F32 threads with VB = 4 own the adjacent units 2t, 2t+1 and read them
+// with one 32-byte load per colour.  Consecutive lanes read consecutive words,
+// across site boundaries too.
 // --------------------------------------------------------------------------
 template <int P> struct VRec;
 
@@ -440,25 +444,31 @@ template <> struct VRec<P_F64> {
     }
 };
 
+// F32: in colour plane c of a site, vectors 2u and 2u + 1 share one 16-byte
+// word {re_2u, re_2u+1, im_2u, im_2u+1}: a load gives the real parts and the
+// imaginary parts of two vectors as aligned register pairs, the operands of
+// the packed FP32 FMAs.  An F32 record group holds an even number of vectors.
 template <> struct VRec<P_F32> {
     typedef float R;
     static constexpr int U = 2;
     static constexpr int SB = 8;
     static __device__ __forceinline__ void load(const char *s, int cs, int w, cpx<float> v[3])
     {
-        const float2 *p = reinterpret_cast<const float2 *>(s) + w;
+        const float *p = reinterpret_cast<const float *>(s) + 2 * (w & ~1) + (w & 1);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float2 a = p[c * cs];
-            v[c].re = a.x;
-            v[c].im = a.y;
+            v[c].re = p[2 * (int64_t)c * cs];
+            v[c].im = p[2 * (int64_t)c * cs + 2];
         }
     }
     static __device__ __forceinline__ void store(char *s, int cs, int w, const cpx<float> v[3])
     {
-        float2 *p = reinterpret_cast<float2 *>(s) + w;
+        float *p = reinterpret_cast<float *>(s) + 2 * (w & ~1) + (w & 1);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p[c * cs] = make_float2(v[c].re, v[c].im);
+        for (int c = 0; c < 3; ++c) {
+            p[2 * (int64_t)c * cs] = v[c].re;
+            p[2 * (int64_t)c * cs + 2] = v[c].im;
+        }
     }
     // unit u = vectors 2u, 2u+1: one 16-byte word per colour
     static __device__ __forceinline__ void load2(const char *s, int cs, int u, cpx<float> a[3], cpx<float> b[3])
@@ -466,10 +476,10 @@ template <> struct VRec<P_F32> {
         const float4 *p = reinterpret_cast<const float4 *>(s) + u;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float4 q = p[c * (cs >> 1)];
+            float4 q = p[(int64_t)c * (cs >> 1)];
             a[c].re = q.x;
-            a[c].im = q.y;
-            b[c].re = q.z;
+            b[c].re = q.y;
+            a[c].im = q.z;
             b[c].im = q.w;
         }
     }
@@ -477,23 +487,41 @@ template <> struct VRec<P_F32> {
     {
         float4 *p = reinterpret_cast<float4 *>(s) + u;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p[c * (cs >> 1)] = make_float4(a[c].re, a[c].im, b[c].re, b[c].im);
+        for (int c = 0; c < 3; ++c) p[(int64_t)c * (cs >> 1)] = make_float4(a[c].re, b[c].re, a[c].im, b[c].im);
+    }
+    // units 2u2, 2u2+1 = vectors 4u2 .. 4u2+3 of colour c as (re, im) pairs of
+    // the vector pairs: re[j] = (re_{4u2+2j}, re_{4u2+2j+1}), im[j] alike.
+    // One 32-byte global load.
+    static __device__ __forceinline__ void load4g_pairs(const char *s, int cs, int u2, int c, float2 re[2],
+                                                        float2 im[2])
+    {
+        const float *p = reinterpret_cast<const float *>(s) + 2 * ((int64_t)c * cs + 4 * u2);
+        asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=f"(re[0].x), "=f"(re[0].y), "=f"(im[0].x), "=f"(im[0].y), "=f"(re[1].x), "=f"(re[1].y),
+                       "=f"(im[1].x), "=f"(im[1].y)
+                     : "l"(p));
+    }
+    static __device__ __forceinline__ void store4g_pairs(char *s, int cs, int u2, int c, const float2 re[2],
+                                                         const float2 im[2])
+    {
+        float *p = reinterpret_cast<float *>(s) + 2 * ((int64_t)c * cs + 4 * u2);
+        asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(re[0].x),
+                     "f"(re[0].y), "f"(im[0].x), "f"(im[0].y), "f"(re[1].x), "f"(re[1].y), "f"(im[1].x), "f"(im[1].y)
+                     : "memory");
     }
     // units 2u2, 2u2+1 = vectors 4u2 .. 4u2+3: one 32-byte global load / store per colour
     static __device__ __forceinline__ void load4g(const char *s, int cs, int u2, cpx<float> v[4][3])
     {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float *p = reinterpret_cast<const float *>(s) + 2 * ((int64_t)c * cs + 4 * u2);
-            float f[8];
-            asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                         : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]),
-                           "=f"(f[7])
-                         : "l"(p));
+            float2 re[2], im[2];
+            load4g_pairs(s, cs, u2, c, re, im);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                v[k][c].re = f[2 * k];
-                v[k][c].im = f[2 * k + 1];
+            for (int j = 0; j < 2; ++j) {
+                v[2 * j][c].re = re[j].x;
+                v[2 * j + 1][c].re = re[j].y;
+                v[2 * j][c].im = im[j].x;
+                v[2 * j + 1][c].im = im[j].y;
             }
         }
     }
@@ -501,26 +529,125 @@ template <> struct VRec<P_F32> {
     {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float *p = reinterpret_cast<float *>(s) + 2 * ((int64_t)c * cs + 4 * u2);
-            asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0][c].re),
-                         "f"(v[0][c].im), "f"(v[1][c].re), "f"(v[1][c].im), "f"(v[2][c].re), "f"(v[2][c].im),
-                         "f"(v[3][c].re), "f"(v[3][c].im)
-                         : "memory");
+            float2 re[2], im[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                re[j] = make_float2(v[2 * j][c].re, v[2 * j + 1][c].re);
+                im[j] = make_float2(v[2 * j][c].im, v[2 * j + 1][c].im);
+            }
+            store4g_pairs(s, cs, u2, c, re, im);
         }
     }
 };
 
+// 16-bit: vectors 2u and 2u + 1 of a site share one 32-byte record of eight
+// 32-bit words: {re_2u, re_2u+1} and {im_2u, im_2u+1} of colours 0, 1, 2 as
+// 16-bit pairs, then the FP32 scales s_2u, s_2u+1 (value = stored number
+// times s; s = max |re|, |im| over the vector's six reals at that site, s = 0
+// storing zeros).  A conversion of one word gives the real or imaginary parts
+// of two vectors as an aligned FP32 pair.  A 16-bit record group holds an even
+// number of vectors.
 template <typename H> struct VRecH {
     typedef float R;
-    static constexpr int U = 1;
+    static constexpr int U = 2;
     static constexpr int SB = 16;
+    // quantise one vector: scale and the six 16-bit values (RN), as the planar format does
+    static __device__ __forceinline__ float quant(const cpx<float> v[3], float q[6])
+    {
+        const float m = fmaxf(fmaxf(fmaxf(fabsf(v[0].re), fabsf(v[0].im)), fmaxf(fabsf(v[1].re), fabsf(v[1].im))),
+                              fmaxf(fabsf(v[2].re), fabsf(v[2].im)));
+        const float inv = m > 0.0f ? 1.0f / m : 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            q[2 * c] = __fmul_rn(v[c].re, inv);
+            q[2 * c + 1] = __fmul_rn(v[c].im, inv);
+        }
+        return m;
+    }
     static __device__ __forceinline__ void load(const char *s, int, int w, cpx<float> v[3])
     {
-        VFmtH<H>::template load<false>(s, 0, w, v);
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(s + (w >> 1) * 32);
+        const int l = w & 1;
+        const float sc = __uint_as_float(p[6 + l]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 re = H2<H>::to2(p[2 * c]), im = H2<H>::to2(p[2 * c + 1]);
+            v[c].re = __fmul_rn(l ? re.y : re.x, sc);
+            v[c].im = __fmul_rn(l ? im.y : im.x, sc);
+        }
     }
     static __device__ __forceinline__ void store(char *s, int, int w, const cpx<float> v[3])
     {
-        VFmtH<H>::template store<false>(s, 0, w, v);
+        float q[6];
+        const float m = quant(v, q);
+        char *b = s + (w >> 1) * 32 + (w & 1) * 2;  // this vector's half of each 16-bit pair
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const uint32_t h = H2<H>::from2(q[k], 0.0f);
+            *reinterpret_cast<unsigned short *>(b + 4 * k) = (unsigned short)(h & 0xffffu);
+        }
+        reinterpret_cast<float *>(s + (w >> 1) * 32)[6 + (w & 1)] = m;
+    }
+    // unit u = vectors 2u, 2u+1: the whole 32-byte record
+    static __device__ __forceinline__ void load2(const char *s, int, int u, cpx<float> a[3], cpx<float> b[3])
+    {
+        float2 re[3], im[3];
+        load_pairs(s, u, re, im);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[c].re = re[c].x;
+            b[c].re = re[c].y;
+            a[c].im = im[c].x;
+            b[c].im = im[c].y;
+        }
+    }
+    static __device__ __forceinline__ void store2(char *s, int, int u, const cpx<float> a[3], const cpx<float> b[3])
+    {
+        float2 re[3], im[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            re[c] = make_float2(a[c].re, b[c].re);
+            im[c] = make_float2(a[c].im, b[c].im);
+        }
+        store_pairs(s, u, re, im);
+    }
+    // unit u as FP32 pairs over its two vectors: re[c] = (re_2u, re_2u+1) of colour c, im[c] alike
+    static __device__ __forceinline__ void load_pairs(const char *s, int u, float2 re[3], float2 im[3])
+    {
+        const uint4 *p = reinterpret_cast<const uint4 *>(s + u * 32);
+        const uint4 x = p[0], y = p[1];
+        const float2 sc = make_float2(__uint_as_float(y.z), __uint_as_float(y.w));
+        re[0] = __fmul2_rn(H2<H>::to2(x.x), sc);
+        im[0] = __fmul2_rn(H2<H>::to2(x.y), sc);
+        re[1] = __fmul2_rn(H2<H>::to2(x.z), sc);
+        im[1] = __fmul2_rn(H2<H>::to2(x.w), sc);
+        re[2] = __fmul2_rn(H2<H>::to2(y.x), sc);
+        im[2] = __fmul2_rn(H2<H>::to2(y.y), sc);
+    }
+    static __device__ __forceinline__ void store_pairs(char *s, int u, const float2 re[3], const float2 im[3])
+    {
+        cpx<float> a[3], b[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[c].re = re[c].x;
+            a[c].im = im[c].x;
+            b[c].re = re[c].y;
+            b[c].im = im[c].y;
+        }
+        float qa[6], qb[6];
+        const float ma = quant(a, qa), mb = quant(b, qb);
+        uint4 x, y;
+        x.x = H2<H>::from2(qa[0], qb[0]);
+        x.y = H2<H>::from2(qa[1], qb[1]);
+        x.z = H2<H>::from2(qa[2], qb[2]);
+        x.w = H2<H>::from2(qa[3], qb[3]);
+        y.x = H2<H>::from2(qa[4], qb[4]);
+        y.y = H2<H>::from2(qa[5], qb[5]);
+        y.z = __float_as_uint(ma);
+        y.w = __float_as_uint(mb);
+        uint4 *p = reinterpret_cast<uint4 *>(s + u * 32);
+        p[0] = x;
+        p[1] = y;
     }
 };
 template <> struct VRec<P_F16> : VRecH<__half> {};
@@ -594,6 +721,9 @@ template <int VP, int VB, bool GM = true> struct RecGroup {
         }
     }
 };
+
+// (re, im) -> (im, re): the second operand pair of a packed complex multiply-add.
+__device__ __forceinline__ float2 f2swap(float2 a) { return make_float2(a.y, a.x); }
 
 // The six +-1 sublattice neighbours of site i (periodic in h).
 __device__ __forceinline__ void sub_neighbours(const SubGeom &g, int i, int fw[3], int bw[3])

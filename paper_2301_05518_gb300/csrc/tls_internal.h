@@ -29,6 +29,7 @@ struct StepArgs {
     int vb;                // vectors per thread
     int threads;           // threads per CTA (multiple of 32)
     int tile[3];           // interleaved kernel: sites per CTA along x', y', z' (0 = a strip along x')
+    int *err;              // device error word (kernels with bounded waits); nullable for the others
     cudaStream_t stream;
 };
 
@@ -141,11 +142,14 @@ cudaError_t launch_pack_il(const void *src, int io_prec, int64_t src_vstride_sit
 cudaError_t launch_unpack_il(const char *src, int prec, void *dst, int io_prec, int64_t dst_vstride_sites,
                              const SubGeom &g, const int L[4], int t_first, int nsl, int nvec, int rec_n, int rec_v0,
                              cudaStream_t s);
-// FP64 |psi|^2 partial sums of nvec canonical vectors (count complex-triplet sites each, vector v at
-// base + v * vstride sites); partials[v][kNormParts], then launch_reduce_norms(partials, kNormParts, ...).
-const int kNormParts = 512;
-cudaError_t launch_norm_partials(const void *base, int io_prec, int64_t vstride_sites, int64_t count, int nvec,
-                                 double *partials, cudaStream_t s);
+// FP64 |psi|^2 partial sums of nvec canonical vectors (vector v at base + v * vstride
+// sites), kNormPartsPerSlice per (vector, slice) over nsl slices of slice_sites sites:
+// partial (v, s, p) at partials[v * part_stride + part_off + s * kNormPartsPerSlice + p].
+// A partial depends only on its slice, so slices may be summed in separate launches;
+// launch_reduce_norms(partials, part_stride, ...) then adds each vector's partials in order.
+const int kNormPartsPerSlice = 16;
+cudaError_t launch_norm_partials(const void *base, int io_prec, int64_t vstride_sites, int64_t slice_sites, int nsl,
+                                 int nvec, double *partials, int64_t part_stride, int64_t part_off, cudaStream_t s);
 // Canonical caller vectors (io_prec F64/F32, slices [t_first, t_first + nsl)) -> packed storage.
 cudaError_t launch_pack_vectors(const void *src, int io_prec, int64_t src_vstride_sites, char *dst, int prec,
                                 int64_t dst_vstride, const SubGeom &g, const int L[4], int t_first, int nsl,

@@ -3,9 +3,9 @@
 // For one problem shape (lattice, slice selection, vector count, storage and
 // W format) it times each candidate kernel over a few steps with CUDA events
 // on the context's launch stream and records the fastest; TLS_KERNEL_AUTO
-// then uses it.  Candidates: the one-vector-per-launch kernel, the
-// interleaved multi-RHS kernel at several CTA sizes, and the persistent
-// kernel at several vectors-per-thread.
+// then uses it.  Candidates: the one-vector-per-launch kernel (up to four
+// vectors) and the multi-right-hand-side kernels that won at some measured
+// shape, at several vectors per thread and CTA shapes.
 #include <algorithm>
 #include <cstring>
 
@@ -20,47 +20,35 @@ struct Cand {
     int tile[3];
 };
 
-std::vector<Cand> candidates(int nvec, int storage, bool rows, bool onchip)
+std::vector<Cand> candidates(int nvec, int storage)
 {
+    // The kernels that won at some measured shape.  Measured and dropped (they
+    // never won at any benchmarked shape): the register-capped and W-staged
+    // interleaved variants, explicit strip lengths, eight vectors per thread in
+    // the packed kernel, the TMA row kernel, the z-marching kernel and both
+    // persistent forms (tls_smear still runs any of them when asked for).
     std::vector<Cand> c;
     if (nvec <= 4) {
         c.push_back({TLS_KERNEL_SINGLE, 1, 128, {0, 0, 0}});
         c.push_back({TLS_KERNEL_SINGLE, 1, 256, {0, 0, 0}});
     }
     const int G = std::min(nvec, 256);
+    const int G2 = storage != TLS_F64 ? (G + 1) & ~1 : G;  // FP32 and 16-bit records come in vector pairs
     for (int vb : {1, 2, 4}) {
-        if (G % vb != 0 || (storage == TLS_F64 && vb > 2)) continue;
-        const int tx = G / vb;
-        for (int t : {64, 128, 256})
-            if (t >= tx || t == 256) c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 0, 0}});
-        if (tx <= 128) c.push_back({TLS_KERNEL_MRHS, vb, -128, {0, 0, 0}});
-        for (int t : {128, 256})  // W of the strip staged in shared memory
-            if (t >= tx) c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 1, 0}});
-        if (storage != TLS_F64)  // packed FP32 pairs with broadcast W in shared memory
-            for (int t : {128, 256})
-                if (t >= tx) {
-                    c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 2, 0}});
-                    c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 4, 0}});  // W as stored, packed FMAs
-                }
-        if (storage != TLS_F64 && tx <= 96)  // packed kernel, register-capped CTAs of <= 96 threads
-            c.push_back({TLS_KERNEL_MRHS, vb, 96, {0, 5, 0}});
-        if (storage != TLS_F64)  // packed kernel with explicit strip lengths
-            for (int spb : {4, 8, 32})
-                if (spb * tx <= 256) c.push_back({TLS_KERNEL_MRHS, vb, 256, {spb, 2, 0}});
-        if (rows) c.push_back({TLS_KERNEL_MRHS_ROWS, vb, 0, {0, 0, 0}});
+        if (G2 % vb != 0 || (storage == TLS_F64 && vb > 2)) continue;
+        if (storage == TLS_F64) {
+            for (int t : {128, 256}) c.push_back({TLS_KERNEL_MRHS, vb, t, {0, 0, 0}});
+            c.push_back({TLS_KERNEL_MRHS, vb, 128, {0, 1, 0}});  // W of the strip staged in shared memory
+            continue;
+        }
+        if (vb == 1 && G2 >= 8) continue;
+        // whole rows with the W rows staged by TMA: all vectors or half of them per CTA
+        c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 6, 0}});
+        c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 7, 0}});
+        if (G2 % 2 == 0 && (G2 / 2) % vb == 0 && G2 / 2 >= 2 * vb) c.push_back({TLS_KERNEL_MRHS, vb, 0, {G2 / 2, 6, 0}});
+        // packed FP32 pairs with the W broadcasts staged by the threads (any row length)
+        c.push_back({TLS_KERNEL_MRHS, vb, 128, {0, 2, 0}});
     }
-    if (storage == TLS_F32 && G % 8 == 0)  // eight FP32 vectors per thread, packed kernel
-        for (int t : {128, 256})
-            if (t >= G / 8) c.push_back({TLS_KERNEL_MRHS, 8, t, {0, 2, 0}});
-    const int vmax = storage == TLS_F64 ? 4 : 8;
-    for (int vb : {1, 4, 8})
-        if (vb <= vmax && (vb == 1 || vb <= 2 * nvec))
-            for (int mb : {48, 96})  // L2 budget of one group of blocks (MB)
-                c.push_back({TLS_KERNEL_PERSISTENT, vb, 256, {mb, 0, 0}});
-    if (onchip)  // every block's W and iterates in one CTA's shared memory
-        for (int vb : {1, 4})
-            if (vb <= vmax)
-                for (int t : {512, 1024}) c.push_back({TLS_KERNEL_PERSISTENT, vb, t, {0, 1, 0}});
     return c;
 }
 
@@ -115,14 +103,7 @@ tls_status tls_autotune(tls_ctx *ctx, tls_gauge_id id, int nvec, int storage, in
     ctx->profiling = true;
     TuneVal win{0, 0, 0, {0, 0, 0}, 1e300};
     int n = 0;
-    const int G = std::min(nvec, 256);
-    const bool rows = storage != TLS_F64 && rows_applicable(gg.wfmt, storage, gg.g, G, 1, ctx->max_smem);
-    int nvg = 0, smem = 0;
-    const bool onchip = onchip_plan(gg.g, wfmt_bytes(gg.wfmt), storage == TLS_F64 ? 48 : 24, nvec, ctx->max_smem,
-                                    &nvg, &smem);
-    for (const Cand &c : candidates(nvec, storage, rows, onchip)) {
-        if (c.kernel == TLS_KERNEL_MRHS_ROWS && !rows_applicable(gg.wfmt, storage, gg.g, G, c.vb, ctx->max_smem))
-            continue;
+    for (const Cand &c : candidates(nvec, storage)) {
         // one warm-up call, then the timed one
         s = smear_impl(ctx, id, tmp, io, 1, nvec, 1, 0.5, timeslice, storage, c.kernel, c.vb, c.threads, c.tile,
                        nullptr, nullptr);

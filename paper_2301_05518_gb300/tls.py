@@ -41,6 +41,7 @@ TLS_KERNEL_AUTO, TLS_KERNEL_SINGLE, TLS_KERNEL_MRHS, TLS_KERNEL_PERSISTENT = 0, 
 TLS_KERNEL_MRHS_ROWS = 4
 TLS_KERNEL_MRHS_ZM = 5
 TLS_ALL_T = -1
+TLS_PEAK_F64, TLS_PEAK_F32, TLS_PEAK_F32X2 = 0, 1, 2
 
 #: every symbol include/tls.h declares
 EXPORTS = (
@@ -48,7 +49,7 @@ EXPORTS = (
     "tls_load_gauge", "tls_build_twolink", "tls_free_gauge", "tls_export_twolink",
     "tls_export_gauge", "tls_smear", "tls_set_profiling", "tls_get_profile",
     "tls_smear_noalloc", "tls_build_links", "tls_ape_smear", "tls_smear_onelink", "tls_set_barrier_budget", "tls_autotune", "tls_tune_set", "tls_serve_start", "tls_serve_stop", "tls_serve_submit",
-    "tls_serve_poll", "tls_serve_wait",
+    "tls_serve_poll", "tls_serve_wait", "tls_peak_flops",
 )
 
 
@@ -118,6 +119,7 @@ def _load() -> ctypes.CDLL:
         "tls_serve_submit": ([P, ctypes.POINTER(tls_job), ctypes.POINTER(U64)], I),
         "tls_serve_poll": ([P, U64, ctypes.POINTER(I)], I),
         "tls_serve_wait": ([P, U64, D, ctypes.POINTER(tls_job_result)], I),
+        "tls_peak_flops": ([I, I, ctypes.POINTER(D)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -319,6 +321,13 @@ def tls_serve_wait(ctx, job_id: int, timeout_s: float = 60.0) -> dict:
 
 
 # ---- a small owner object ------------------------------------------------------
+def tls_peak_flops(device: int, kind: int) -> float:
+    """Measured arithmetic rate of the GPU in TFLOP/s (TLS_PEAK_F64 / F32 / F32X2)."""
+    out = ctypes.c_double(0.0)
+    _check(lib.tls_peak_flops(device, kind, ctypes.byref(out)))
+    return out.value
+
+
 class Context:
     """Owns a tls_ctx; the methods are the C entry points minus the prefix."""
 

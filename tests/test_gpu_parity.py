@@ -216,6 +216,37 @@ def test_host_buffers_match_device(ctx, T, kern):
         assert np.array_equal(nd, nh) and np.array_equal(nd, npn)
 
 
+@pytest.mark.parametrize("kern,storage,nvec", [("MRHS", "F32", 5), ("SINGLE", "F32", 2), ("PERSISTENT", "F32", 3),
+                                                ("MRHS", "F16", 4), ("MRHS", "F64", 3)])
+def test_host_pipeline_slice_groups(ctx, T, kern, storage, nvec):
+    """Host vectors through the slice-group pipeline (7 slices: 4 groups of 2, 2, 2, 1 slices in
+    three rotating staging slots, copies overlapping the smearing) == device vectors, bitwise,
+    norms included; also for one slice."""
+    dims = (8, 4, 6, 7)
+    U = gauge(dims, "haar", 23)
+    vecs = synth.gaussian_vectors(dims, nvec, 24)
+    st = getattr(T, "TLS_" + storage)
+    wp = T.TLS_F64 if storage == "F64" else T.TLS_F32
+    k = getattr(T, "TLS_KERNEL_" + kern)
+    for t0 in (-1, 5):
+        dev, nd = _run(ctx, T, U, dims, vecs, st, wp, 18, k, 4, 1.1, t0)
+        host, nh = _run(ctx, T, U, dims, vecs, st, wp, 18, k, 4, 1.1, t0, host="pinned")
+        assert np.array_equal(dev, host)
+        assert np.array_equal(nd, nh)
+
+
+def test_host_gauge_load_two_slots(ctx, T):
+    """A host gauge field of more than one staging slot (20 slices of 32^3: the spatial links
+    copied by 2-D copies in groups through two slots) ingests bit-exactly."""
+    dims = (32, 32, 32, 20)
+    U = synth.gauge_haar(dims, 25, nd=4)
+    gid = ctx.load_gauge(U, 4, dims)
+    out = np.zeros(U.shape[:4] + (3, 3, 3), dtype=np.complex128)
+    ctx.export_gauge(gid, out)
+    ctx.free_gauge(gid)
+    assert np.array_equal(out, U.numpy()[..., :3, :, :])
+
+
 def test_two_site_extent(ctx, T):
     """L = 2 in every direction: the hop returns to the same site through W and W^dag."""
     dims = (2, 2, 2, 2)
@@ -354,7 +385,8 @@ def test_autotune_picks_a_working_kernel(ctx, T):
     best, cands = ctx.autotune(gid, 5, T.TLS_F32, T.TLS_ALL_T, steps=3)
     assert len(cands) >= 3 and best["ms_per_step"] == min(c["ms_per_step"] for c in cands)
     kinds = {c["kernel"] for c in cands}
-    assert {T.TLS_KERNEL_MRHS, T.TLS_KERNEL_PERSISTENT} <= kinds
+    assert T.TLS_KERNEL_MRHS in kinds and T.TLS_KERNEL_PERSISTENT not in kinds  # retired from the tuner
+    assert any(tuple(c["tile"])[1] == 6 for c in cands)  # the TMA row kernel is a candidate
     x = vecs.clone().cuda()
     ctx.set_profiling(True)
     ctx.smear(gid, x, T.TLS_F32, 5, 6, 1.2)  # AUTO uses the table entry
@@ -428,11 +460,16 @@ def test_rows_kernel_at_headline_shape_sampled(ctx, T):
                                              ((3, 3, 0), 1, "F32"), ((0, 3, 0), 4, "BF16"), ((0, 4, 0), 2, "F32"),
                                              ((5, 4, 0), 4, "F16"), ((3, 4, 0), 1, "BF16"), ((0, 4, 0), 4, "F32"),
                                              ((0, 2, 0), 8, "F32"), ((3, 2, 0), 8, "F32"), ((0, 5, 0), 4, "F32"),
-                                             ((0, 5, 0), 2, "F16"), ((5, 5, 0), 1, "BF16")])
+                                             ((0, 5, 0), 2, "F16"), ((5, 5, 0), 1, "BF16"),
+                                             ((0, 6, 0), 4, "F32"), ((0, 6, 0), 2, "F32"), ((0, 6, 0), 1, "F32"),
+                                             ((4, 6, 0), 4, "F32"), ((2, 6, 0), 2, "F32"), ((0, 6, 0), 2, "F16"),
+                                             ((0, 6, 0), 4, "BF16"), ((4, 6, 0), 4, "F16"), ((0, 7, 0), 4, "F32"),
+                                             ((0, 7, 0), 1, "BF16"), ((0, 6, 0), 8, "F32")])
 @pytest.mark.parametrize("recon", [18, 12])
 def test_interleaved_strips_bitwise_equal_single(ctx, T, tile, vb, storage, recon):
-    """Strip lengths (some not dividing hx), W staged in shared memory (tile[1] = 1) and the
-    packed FP32 pair kernel (tile[1] = 2) == one vector per launch, bitwise."""
+    """Strip lengths (some not dividing hx), W staged in shared memory (tile[1] = 1), the
+    packed FP32 pair kernel (tile[1] = 2) and the whole-row kernel with TMA-staged W rows
+    (tile[1] = 6, 7; tile[0] = vectors per CTA) == one vector per launch, bitwise."""
     dims = (12, 10, 8, 2)
     nvec = 8
     st = getattr(T, "TLS_" + storage)
@@ -453,6 +490,38 @@ def test_interleaved_strips_bitwise_equal_single(ctx, T, tile, vb, storage, reco
     if storage == "F32" and recon == 18:
         want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), 6, 1.3)
         assert max(per_vector_rel_l2(a.cpu().numpy().astype(np.complex128), want)) <= 2e-6 * 6
+
+
+@pytest.mark.parametrize("dims,nvec,storage,wprec,recon,vb,nvg", [
+    ((8, 8, 8, 3), 24, "F32", "F32", 18, 4, 0), ((16, 8, 12, 2), 24, "F32", "F32", 18, 4, 12),
+    ((8, 16, 24, 2), 8, "F32", "F32", 12, 2, 0), ((12, 8, 8, 2), 12, "F32", "F32", 8, 4, 4),
+    ((8, 8, 8, 2), 6, "F16", "F16", 12, 2, 0), ((16, 8, 8, 2), 8, "BF16", "BF16", 18, 4, 0),
+    ((8, 4, 4, 2), 16, "F16", "F32", 18, 4, 8), ((10, 6, 4, 2), 4, "F16", "F16", 18, 2, 0),
+    ((10, 6, 4, 2), 4, "F32", "F32", 18, 4, 0), ((2, 2, 2, 1), 4, "F32", "F32", 18, 4, 0),
+    ((4, 4, 2, 2), 3, "F32", "F32", 18, 1, 0)])
+def test_row_tma_kernel_bitwise_equal_single(ctx, T, dims, nvec, storage, wprec, recon, vb, nvg):
+    """Whole-row CTAs with the five W rows staged by TMA bulk copies (tile[1] = 6, 7) == one
+    vector per launch, bitwise, on every slice and on one slice; hx = 5 with a 4- or 8-byte W
+    remainder plane takes the packed kernel instead (same results)."""
+    U = gauge(dims, "haar", 37)
+    vecs = synth.gaussian_vectors(dims, nvec, 38, dtype=torch.complex64)
+    st = getattr(T, "TLS_" + storage)
+    wp = getattr(T, "TLS_" + wprec)
+    gid = ctx.load_gauge(U, 4, dims)
+    ctx.build_twolink(gid, wp, recon)
+    for t0 in (-1, dims[3] - 1):
+        b = vecs.clone().cuda()
+        ctx.smear(gid, b, T.TLS_F32, nvec, 7, 1.4, timeslice=t0, storage=st, kernel=T.TLS_KERNEL_SINGLE)
+        for variant in (6, 7):  # one CTA per row, registers capped for 3 or 2 CTAs of 256 threads
+            ctx.tune_set(gid, nvec, st, t0, T.TLS_KERNEL_MRHS, vb, 0, (nvg, variant, 0))
+            a = vecs.clone().cuda()
+            ctx.smear(gid, a, T.TLS_F32, nvec, 7, 1.4, timeslice=t0, storage=st, kernel=T.TLS_KERNEL_AUTO)
+            assert torch.equal(a, b), variant
+    ctx.free_gauge(gid)
+    if storage == "F32" and recon == 18:  # the last slice (smeared alone) against the oracle
+        want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), 7, 1.4)
+        got = a.cpu().numpy().astype(np.complex128)
+        assert max(per_vector_rel_l2(got[:, -1:], want[:, -1:])) <= 2e-6 * 7
 
 
 # ------------------------------------------------------------------ one-link Gaussian smearing (Eq. 2-3)

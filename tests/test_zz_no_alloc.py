@@ -1,8 +1,8 @@
 """tls_smear_noalloc: the smear for callers that cannot allocate device memory.
 
-Some callers may not call cudaMalloc while they run: code inside a CUDA
-stream capture, a latency-critical thread (cudaFree synchronises the device),
-or a process whose device memory belongs to another allocator.  This entry
+Some callers may not call cudaMalloc while they run: a latency-critical
+thread (cudaFree synchronises the device), or a process whose device memory
+belongs to another allocator.  This entry
 point keeps all its intermediate data in a fixed static device array owned by
 the library.  The test calls it through the C ABI twice in a row and checks
 each result against tls_smear with the persistent kernel (the existing entry
@@ -43,11 +43,25 @@ def test_noalloc_matches_persistent_smear_twice(T):
             got = vecs.clone()
             torch.cuda.synchronize()
             before = ctx.bytes_in_use()
+            free_before = torch.cuda.mem_get_info()[0]
             ctx.smear_noalloc(gid, got, T.TLS_F32, 3, N, sigma, storage=T.TLS_F32)
             assert ctx.bytes_in_use() == before
+            if call > 0:  # warmed up: the device's free memory does not move either
+                assert torch.cuda.mem_get_info()[0] == free_before
             errs = per_vector_rel_l2(got.cpu().numpy().astype(np.complex128),
                                      ref.cpu().numpy().astype(np.complex128))
             assert max(errs) <= 2e-6 * N, (call, errs)
+        # one slice, FP32; then 16-bit storage with its per-site scales (FP32 scratch)
+        for storage, t0, tol in ((T.TLS_F32, 1, 2e-6 * N), (T.TLS_F16, -1, 5e-3), (T.TLS_BF16, 3, 5e-3)):
+            vecs = synth.gaussian_vectors(dims, 4, 96 + storage, dtype=torch.complex64).cuda()
+            ref = vecs.clone()
+            ctx.smear(gid, ref, T.TLS_F32, 4, N, sigma, timeslice=t0, storage=storage,
+                      kernel=T.TLS_KERNEL_PERSISTENT)
+            got = vecs.clone()
+            ctx.smear_noalloc(gid, got, T.TLS_F32, 4, N, sigma, timeslice=t0, storage=storage)
+            errs = per_vector_rel_l2(got.cpu().numpy().astype(np.complex128),
+                                     ref.cpu().numpy().astype(np.complex128))
+            assert max(errs) <= tol, (storage, t0, errs)
         # one slice only, FP64
         ctx.build_twolink(gid, T.TLS_F64, T.TLS_R18)
         vecs = synth.gaussian_vectors(dims, 2, 94).cuda()
