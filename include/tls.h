@@ -104,8 +104,10 @@ uint64_t tls_bytes_in_use(const tls_ctx *ctx);
 /* ---- gauge field ingest (Sec. 2: U_mu(x)) ----------------------------------
  * Copies the spatial links of U (layout above, FP64) to the device and
  * permutes them into the library's sublattice layout (bit-exact).  U is a
- * device pointer if on_device != 0, else a host pointer; the caller keeps
- * ownership and may free it when the call returns.  The work is enqueued on
+ * device pointer if on_device != 0, else a host pointer (only the spatial
+ * links are copied, in slice groups whose copy overlaps the permutation of
+ * the previous group); the caller keeps ownership and may free it when the
+ * call returns.  The work is enqueued on
  * `stream` and finished before return.  Returns the new id in *out.
  * Errors: TLS_ERR_ARG (nd not 3/4, odd or non-positive extent, more than
  * 2^31 sites), TLS_ERR_ADMIT, TLS_ERR_NOMEM, TLS_ERR_CUDA.                  */
@@ -171,8 +173,12 @@ tls_status tls_export_gauge(tls_ctx *ctx, tls_gauge_id id, double *out, int on_d
  * timeslice in [0, Lt) smears that slice only and leaves the other slices of
  * `vecs` untouched; TLS_ALL_T smears every slice.
  *   vecs            caller's vectors, layout above, io_prec TLS_F64 or TLS_F32;
- *                   device pointer if vecs_on_device != 0, else host pointer
- *                   (then the host<->device copies happen inside the call).
+ *                   device pointer if vecs_on_device != 0, else host pointer:
+ *                   then the slices go through the device in groups of about
+ *                   2 GB, the copy of one group in, the smearing of another
+ *                   and the copy of a third back out overlapping on three
+ *                   streams (pinned host memory lets the copies run at full
+ *                   speed).
  *   storage         precision the iterates are stored in between steps:
  *                   TLS_F64 (needs an FP64 W), TLS_F32 (FP32 W), TLS_F16 or
  *                   TLS_BF16 (FP32 or 16-bit W; one FP32 scale per site and
@@ -279,6 +285,11 @@ typedef struct {
                             /* tile[1] = 4 stages W as stored and applies it   */
                             /* with packed FP32 pair FMAs, tile[1] = 5 is 2    */
                             /* held to 56 registers in CTAs of <= 96 threads;  */
+                            /* tile[1] = 6 runs one CTA per whole x'-row with  */
+                            /* the row's five W rows copied in by TMA bulk     */
+                            /* copies (tile[0] > 0: vectors per CTA), 7 the    */
+                            /* same with a looser register cap (FP32 and       */
+                            /* 16-bit storage; other shapes take tile[1] = 2); */
                             /* tile[2] unused                                  */
     double ms_per_step;     /* measured time of one smearing step              */
 } tls_tune_entry;

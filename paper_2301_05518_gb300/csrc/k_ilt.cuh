@@ -78,7 +78,7 @@ __device__ __forceinline__ void ilt_issue_w(char *ws, const char *__restrict__ W
 // One thread's part of a row: site x' = k of row (blk, zq, yq), vector units
 // t of T (VB vectors each), W rows staged at ws.  pl holds the records of the
 // first hop (requested before the wait on the copies).
-template <int VP, int WF, int VB, bool ACT> struct IltSite {
+template <int VP, int WF, int VB, bool ACT, bool PF = false> struct IltSite {
     int nb[6];  // the six hops in the order of site_step
     int i;
     const char *rin;
@@ -96,7 +96,8 @@ template <int VP, int WF, int VB, bool ACT> struct IltSite {
     cpx<float> pl[PAIRS ? 1 : VB][3];
 
     // the records of this thread's vectors at site pointer s
-    __device__ __forceinline__ void load_rec(const char *s)
+    __device__ __forceinline__ void load_rec(const char *s) { load_rec_to(s, pre, pim); }
+    __device__ __forceinline__ void load_rec_to(const char *s, float2 (&pre)[NP][3], float2 (&pim)[NP][3])
     {
         if constexpr (PAIRS && VP != P_F32) {  // 16-bit: one 32-byte record per pair, dequantised
 #pragma unroll
@@ -157,16 +158,130 @@ template <int VP, int WF, int VB, bool ACT> struct IltSite {
         }
         tt = t;
         TT = T;
-        if (any) load_rec(rin + (unsigned)nb[0] * rstride);
+        if (any) {
+            if constexpr (COLS)
+                load_col(rin + (unsigned)nb[0] * rstride, 0, pre0, pim0);
+            else
+                load_rec(rin + (unsigned)nb[0] * rstride);
+        }
+    }
+
+    // FP32 with VB = 8: records are read one colour at a time (two 32-byte
+    // loads), so only one colour of the four vector pairs is live.
+    static constexpr bool COLS = VP == P_F32 && VB == 8;
+    float2 pre0[COLS ? 4 : 1], pim0[COLS ? 4 : 1];  // colour 0 of the first hop
+    __device__ __forceinline__ void load_col(const char *s, int c, float2 re[4], float2 im[4])
+    {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) VRec<P_F32>::load4g_pairs(s, cs, 2 * tt + j, c, re + 2 * j, im + 2 * j);
     }
 
     __device__ __forceinline__ void compute(const char *ws, int hx, int k, int t, int T,
                                             const float *__restrict__ alphaf)
     {
-        if constexpr (PAIRS)
+        if constexpr (COLS)
+            compute_cols(ws, hx, k, t, T, alphaf);
+        else if constexpr (PAIRS)
             compute_pairs(ws, hx, k, t, T, alphaf);
         else
             compute_cpx(ws, hx, k, t, T, alphaf);
+    }
+
+    // The element of the stored W matrix the hop uses for row r, column c.
+    __device__ __forceinline__ cpx<float> w_elem(const char *wset, int hx, int wk, const cpx<float> *m, bool dag,
+                                                 int r, int c)
+    {
+        cpx<float> w;
+        if constexpr (WF == W_F32_18) {
+            // element e of a stored f32-18 matrix: one 8-byte word, read when used
+            const int e = dag ? c * 3 + r : r * 3 + c;
+            const float2 f = e < 8 ? reinterpret_cast<const float2 *>(wset)[((e >> 1) * hx + wk) * 2 + (e & 1)]
+                                   : reinterpret_cast<const float2 *>(wset + 4 * hx * 16)[wk];
+            w.re = f.x;
+            w.im = f.y;
+        } else {
+            w = dag ? m[c * 3 + r] : m[r * 3 + c];
+        }
+        return w;
+    }
+
+    // compute_pairs for FP32 with VB = 8, one colour of the records at a time.
+    __device__ __forceinline__ void compute_cols(const char *ws, int hx, int k, int t, int T,
+                                                 const float *__restrict__ alphaf)
+    {
+        constexpr int WB = wfmt_bytes(WF);
+        const int setB = hx * WB;
+        float2 accR[4][3], accI[4][3];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) accR[j][r] = accI[j][r] = make_float2(0.f, 0.f);
+        const int km = k == 0 ? hx - 1 : k - 1;
+        const float2 neg1 = make_float2(-1.f, -1.f);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const bool dag = q & 1;
+            const char *rs = rin + (unsigned)nb[q] * rstride;
+            const char *wset = ws + (q == 0 ? 0 : q - 1) * setB;
+            const int wk = q == 1 ? km : k;
+            cpx<float> m[WF == W_F32_18 ? 1 : 9];
+            if constexpr (WF != W_F32_18) WFmt<WF>::load(wset, hx, wk, m);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float2 re[4], im[4], ng[4];
+                if (q == 0 && c == 0) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        re[j] = pre0[j];
+                        im[j] = pim0[j];
+                    }
+                } else {
+                    load_col(rs, c, re, im);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ng[j] = __fmul2_rn(dag ? re[j] : im[j], neg1);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const cpx<float> w = w_elem(wset, hx, wk, m, dag, r, c);
+                    const float2 wr = make_float2(w.re, w.re), wi = make_float2(w.im, w.im);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        accR[j][r] = __ffma2_rn(wr, re[j], accR[j][r]);
+                        accR[j][r] = __ffma2_rn(wi, dag ? im[j] : ng[j], accR[j][r]);
+                        accI[j][r] = __ffma2_rn(wr, im[j], accI[j][r]);
+                        accI[j][r] = __ffma2_rn(wi, dag ? ng[j] : re[j], accI[j][r]);
+                    }
+                }
+            }
+        }
+        const float2 m6 = make_float2(-6.f, -6.f);
+        float2 a2[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a2[j] = *reinterpret_cast<const float2 *>(alphaf + il_vec<VP, VB>(t, T, 2 * j));
+        const char *sc = rin + (unsigned)i * rstride;
+        char *so = rout + (unsigned)i * rstride;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float2 re[4], im[4];
+            load_col(sc, c, re, im);  // the centre
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                re[j] = __ffma2_rn(a2[j], __ffma2_rn(m6, re[j], accR[j][c]), re[j]);
+                im[j] = __ffma2_rn(a2[j], __ffma2_rn(m6, im[j], accI[j][c]), im[j]);
+            }
+            if (all) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) VRec<P_F32>::store4g_pairs(so, cs, 2 * t + j, c, re + 2 * j, im + 2 * j);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 8; ++v)
+                    if (on[v]) {
+                        float *p = reinterpret_cast<float *>(so) + 2 * ((int64_t)c * cs + (8 * t + (v & ~1))) + (v & 1);
+                        p[0] = (v & 1) ? re[v >> 1].y : re[v >> 1].x;
+                        p[2] = (v & 1) ? im[v >> 1].y : im[v >> 1].x;
+                    }
+            }
+        }
     }
 
     // FP32 storage.  Per element w of a hop and vector pair j, with the negated
@@ -175,11 +290,14 @@ template <int VP, int WF, int VB, bool ACT> struct IltSite {
     //   backward conj W(c, r):  R += {wr} re;  R += {wi} im;     I += {wr} im;  I += {wi} (-re)
     // ({x} = the pair (x, x)): lane by lane the FMA sequence of cmac / cmacc,
     // products with a negated factor being exact negations.
+    // PF: the records of hop q + 1 (the centre after hop 5) are requested
+    // before hop q is applied, two record buffers alternating.
     __device__ __forceinline__ void compute_pairs(const char *ws, int hx, int k, int t, int T,
                                                   const float *__restrict__ alphaf)
     {
         constexpr int WB = wfmt_bytes(WF);
         const int setB = hx * WB;
+        float2 qre[NP][3], qim[NP][3];  // the other buffer of the prefetch
         float2 accR[NP][3], accI[NP][3];
 #pragma unroll
         for (int j = 0; j < NP; ++j)
@@ -189,7 +307,17 @@ template <int VP, int WF, int VB, bool ACT> struct IltSite {
         const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-            if (q > 0) load_rec(rin + (unsigned)nb[q] * rstride);
+            if constexpr (PF) {
+                const char *nx = rin + (unsigned)(q < 5 ? nb[q + 1] : i) * rstride;
+                if (q & 1)
+                    load_rec_to(nx, pre, pim);
+                else
+                    load_rec_to(nx, qre, qim);
+            } else if (q > 0) {
+                load_rec(rin + (unsigned)nb[q] * rstride);
+            }
+            float2 (&cre)[NP][3] = (PF && (q & 1)) ? qre : pre;
+            float2 (&cim)[NP][3] = (PF && (q & 1)) ? qim : pim;
             const bool dag = q & 1;
             const char *wset = ws + (q == 0 ? 0 : q - 1) * setB;
             const int wk = q == 1 ? km : k;
@@ -199,7 +327,7 @@ template <int VP, int WF, int VB, bool ACT> struct IltSite {
             for (int c = 0; c < 3; ++c) {
                 float2 ng[NP];
 #pragma unroll
-                for (int j = 0; j < NP; ++j) ng[j] = __fmul2_rn(dag ? pre[j][c] : pim[j][c], neg1);
+                for (int j = 0; j < NP; ++j) ng[j] = __fmul2_rn(dag ? cre[j][c] : cim[j][c], neg1);
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
                     cpx<float> w;
@@ -216,15 +344,15 @@ template <int VP, int WF, int VB, bool ACT> struct IltSite {
                     const float2 wr = make_float2(w.re, w.re), wi = make_float2(w.im, w.im);
 #pragma unroll
                     for (int j = 0; j < NP; ++j) {
-                        accR[j][r] = __ffma2_rn(wr, pre[j][c], accR[j][r]);
-                        accR[j][r] = __ffma2_rn(wi, dag ? pim[j][c] : ng[j], accR[j][r]);
-                        accI[j][r] = __ffma2_rn(wr, pim[j][c], accI[j][r]);
-                        accI[j][r] = __ffma2_rn(wi, dag ? ng[j] : pre[j][c], accI[j][r]);
+                        accR[j][r] = __ffma2_rn(wr, cre[j][c], accR[j][r]);
+                        accR[j][r] = __ffma2_rn(wi, dag ? cim[j][c] : ng[j], accR[j][r]);
+                        accI[j][r] = __ffma2_rn(wr, cim[j][c], accI[j][r]);
+                        accI[j][r] = __ffma2_rn(wi, dag ? ng[j] : cre[j][c], accI[j][r]);
                     }
                 }
             }
         }
-        load_rec(rin + (unsigned)i * rstride);  // the centre
+        if constexpr (!PF) load_rec(rin + (unsigned)i * rstride);  // the centre (PF: loaded during hop 5)
         const float2 m6 = make_float2(-6.f, -6.f);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
@@ -270,7 +398,7 @@ template <int VP, int WF, int VB, bool ACT> struct IltSite {
                         o[c].re = (v & 1) ? pre[v >> 1][c].y : pre[v >> 1][c].x;
                         o[c].im = (v & 1) ? pim[v >> 1][c].y : pim[v >> 1][c].x;
                     }
-                    VRec<P_F32>::store(so, cs, il_vec<VP, VB>(t, T, v), o);
+                    VRec<VP>::store(so, cs, il_vec<VP, VB>(t, T, v), o);
                 }
         }
     }
@@ -349,38 +477,58 @@ __device__ __forceinline__ bool ilt_wait(uint64_t *bar, unsigned parity)
     return true;
 }
 
-template <int VP, int WF, int VB, bool ACT, int MAXT, int MINB>
+// nrow consecutive rows y' = blockIdx.y * nrow + r per CTA: the W rows of all
+// of them are copied at the start (one mbarrier per row), so only the first
+// row waits for its copies; the others find theirs landed.
+template <int VP, int WF, int VB, bool ACT, int MAXT, int MINB, bool PF = false>
 __global__ void __launch_bounds__(MAXT, MINB) k_step_ilt(const char *__restrict__ W, const char *__restrict__ in,
                                                         char *__restrict__ out, const float *__restrict__ alphaf,
-                                                        const int *__restrict__ active, SubGeom g, int nvec, int *err)
+                                                        const int *__restrict__ active, SubGeom g, int nvec, int nrow,
+                                                        int *err)
 {
     static_assert(VP != P_F64, "packed FP32 pairs only");
+    constexpr int WB = wfmt_bytes(WF);
     extern __shared__ __align__(128) unsigned char ilt_sm[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(ilt_sm);
-    char *ws = reinterpret_cast<char *>(ilt_sm) + 128;
-    const int yq = blockIdx.y;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ilt_sm);  // one per row (nrow <= 16)
+    char *ws0 = reinterpret_cast<char *>(ilt_sm) + 128;
+    const int setsB = 5 * g.hx * WB;
+    const int y0 = blockIdx.y * nrow;
     const int blk = blockIdx.z / g.hz;
     const int zq = blockIdx.z - blk * g.hz;
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
     if (leader) {
-        mbar_init(bar, 1);
+        for (int r = 0; r < nrow; ++r) mbar_init(&bar[r], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (leader) ilt_issue_w<WF>(ws, W, g, blk, zq, yq, bar);
+    if (leader)
+        for (int r = 0; r < nrow; ++r) ilt_issue_w<WF>(ws0 + r * setsB, W, g, blk, zq, y0 + r, &bar[r]);
 
     const int k = threadIdx.y;                           // x' of this thread's site
     const int t = blockIdx.x * blockDim.x + threadIdx.x;  // vector unit over the whole site
     const int T = nvec / VB;
-    IltSite<VP, WF, VB, ACT> st;
-    st.setup(in, out, active, g, nvec, blk, zq, yq, k, t, T);
-    // every thread waits: the CTA must not retire while its copies are in flight
-    if (!ilt_wait(bar, 0u)) {
-        if (leader) atomicOr(err, DERR_TIMEOUT);
-        ilt_wait(bar, 0u);  // once more (bounded) for the copies in flight
-        return;
+    __shared__ int w_ok;
+    for (int r = 0; r < nrow; ++r) {
+        IltSite<VP, WF, VB, ACT, PF> st;
+        st.setup(in, out, active, g, nvec, blk, zq, y0 + r, k, t, T);
+        // The first warp waits for the row's copies; the others wait at the
+        // CTA barrier without spending issue slots.  The CTA must not retire
+        // while its copies are in flight: on a timeout the leader waits once
+        // more (bounded) for every row still pending.
+        if (threadIdx.x + threadIdx.y * blockDim.x < 32) {
+            const bool okw = ilt_wait(&bar[r], 0u);
+            if (leader) {
+                w_ok = okw;
+                if (!okw) {
+                    atomicOr(err, DERR_TIMEOUT);
+                    for (int q = r; q < nrow; ++q) ilt_wait(&bar[q], 0u);
+                }
+            }
+        }
+        __syncthreads();
+        if (!w_ok) return;
+        if (st.any) st.compute(ws0 + r * setsB, g.hx, k, t, T, alphaf);
     }
-    if (st.any) st.compute(ws, g.hx, k, t, T, alphaf);
 }
 
 // Vectors per CTA: tile[0] if it is a multiple of VB dividing nvec, else the
@@ -394,44 +542,49 @@ inline int ilt_group(int nvec, int vb, int hx, int want)
     return 0;
 }
 
-// tile[1] = 6: registers capped for 3 CTAs of 256 threads per SM; 7: for 3 CTAs of
-// 192 threads (2 of 256 when the row needs more threads).
+// tile[1] = 6: registers capped for 3 CTAs of 256 threads per SM; 7: the next
+// hop's records prefetched, registers for 3 CTAs of 192 threads (2 of 256
+// when the row needs more threads).
 template <int VP, int WF, int VB> cudaError_t ilt_launch(const StepArgs &a)
 {
-    if constexpr (VP == P_F64 || VB > 4) {
+    if constexpr (VP == P_F64 || (VB > 4 && !(VP == P_F32 && VB == 8))) {
         return cudaErrorNotSupported;
     } else {
         if (!a.err || !a.alphaf || !ilt_ok(WF, a.g)) return cudaErrorNotSupported;
         const int nvg = ilt_group(a.nvec, VB, a.g.hx, a.tile[0]);
         if (nvg == 0) return cudaErrorNotSupported;
+        // tile[2] = rows per CTA (1 by default; it must divide hy and fit the shared memory)
+        int nrow = a.tile[2] > 0 ? std::min(a.tile[2], 16) : 1;
+        while (nrow > 1 && (a.g.hy % nrow != 0 || 128 + nrow * (ilt_smem(a.g.hx, wfmt_bytes(WF)) - 128) > (48 << 10)))
+            --nrow;
         dim3 block(nvg / VB, a.g.hx);
-        dim3 grid(a.nvec / nvg, a.g.hy, (unsigned)a.g.hz * a.nblk);
+        dim3 grid(a.nvec / nvg, a.g.hy / nrow, (unsigned)a.g.hz * a.nblk);
         if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-        const int smem = ilt_smem(a.g.hx, wfmt_bytes(WF));
+        const int smem = 128 + nrow * (ilt_smem(a.g.hx, wfmt_bytes(WF)) - 128);
         if (smem > (48 << 10)) return cudaErrorNotSupported;
         const bool act = a.active != nullptr;
         const int threads = block.x * block.y;
         if (a.tile[1] == 7 && threads <= 192) {  // registers for 3 CTAs of 192 threads per SM
             if (act)
-                k_step_ilt<VP, WF, VB, true, 192, 3><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
+                k_step_ilt<VP, WF, VB, true, 192, 3, true><<<grid, block, smem, a.stream>>>(
+                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, nrow, a.err);
             else
-                k_step_ilt<VP, WF, VB, false, 192, 3><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
+                k_step_ilt<VP, WF, VB, false, 192, 3, true><<<grid, block, smem, a.stream>>>(
+                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, nrow, a.err);
         } else if (a.tile[1] == 7) {  // registers for 2 CTAs of 256 threads per SM
             if (act)
-                k_step_ilt<VP, WF, VB, true, 256, 2><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
+                k_step_ilt<VP, WF, VB, true, 256, 2, true><<<grid, block, smem, a.stream>>>(
+                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, nrow, a.err);
             else
-                k_step_ilt<VP, WF, VB, false, 256, 2><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
+                k_step_ilt<VP, WF, VB, false, 256, 2, true><<<grid, block, smem, a.stream>>>(
+                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, nrow, a.err);
         } else {  // registers for 3 CTAs of 256 threads per SM
             if (act)
                 k_step_ilt<VP, WF, VB, true, 256, 3><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
+                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, nrow, a.err);
             else
                 k_step_ilt<VP, WF, VB, false, 256, 3><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
+                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, nrow, a.err);
         }
         return cudaGetLastError();
     }

@@ -592,7 +592,7 @@ template <typename H> struct VRecH {
     static __device__ __forceinline__ void load2(const char *s, int, int u, cpx<float> a[3], cpx<float> b[3])
     {
         float2 re[3], im[3];
-        load_pairs(s, u, re, im);
+        load_pairs<false>(s, u, re, im);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             a[c].re = re[c].x;
@@ -609,13 +609,23 @@ template <typename H> struct VRecH {
             re[c] = make_float2(a[c].re, b[c].re);
             im[c] = make_float2(a[c].im, b[c].im);
         }
-        store_pairs(s, u, re, im);
+        store_pairs<false>(s, u, re, im);
     }
     // unit u as FP32 pairs over its two vectors: re[c] = (re_2u, re_2u+1) of colour c, im[c] alike
+    // GM: s is global memory (one 32-byte load / store per record)
+    template <bool GM = true>
     static __device__ __forceinline__ void load_pairs(const char *s, int u, float2 re[3], float2 im[3])
     {
-        const uint4 *p = reinterpret_cast<const uint4 *>(s + u * 32);
-        const uint4 x = p[0], y = p[1];
+        uint4 x, y;
+        if constexpr (GM) {
+            asm volatile("ld.global.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(x.x), "=r"(x.y), "=r"(x.z), "=r"(x.w), "=r"(y.x), "=r"(y.y), "=r"(y.z), "=r"(y.w)
+                         : "l"(s + u * 32));
+        } else {
+            const uint4 *p = reinterpret_cast<const uint4 *>(s + u * 32);
+            x = p[0];
+            y = p[1];
+        }
         const float2 sc = make_float2(__uint_as_float(y.z), __uint_as_float(y.w));
         re[0] = __fmul2_rn(H2<H>::to2(x.x), sc);
         im[0] = __fmul2_rn(H2<H>::to2(x.y), sc);
@@ -624,6 +634,7 @@ template <typename H> struct VRecH {
         re[2] = __fmul2_rn(H2<H>::to2(y.x), sc);
         im[2] = __fmul2_rn(H2<H>::to2(y.y), sc);
     }
+    template <bool GM = true>
     static __device__ __forceinline__ void store_pairs(char *s, int u, const float2 re[3], const float2 im[3])
     {
         cpx<float> a[3], b[3];
@@ -645,9 +656,15 @@ template <typename H> struct VRecH {
         y.y = H2<H>::from2(qa[5], qb[5]);
         y.z = __float_as_uint(ma);
         y.w = __float_as_uint(mb);
-        uint4 *p = reinterpret_cast<uint4 *>(s + u * 32);
-        p[0] = x;
-        p[1] = y;
+        if constexpr (GM) {
+            asm volatile("st.global.v8.u32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(s + u * 32), "r"(x.x),
+                         "r"(x.y), "r"(x.z), "r"(x.w), "r"(y.x), "r"(y.y), "r"(y.z), "r"(y.w)
+                         : "memory");
+        } else {
+            uint4 *p = reinterpret_cast<uint4 *>(s + u * 32);
+            p[0] = x;
+            p[1] = y;
+        }
     }
 };
 template <> struct VRec<P_F16> : VRecH<__half> {};

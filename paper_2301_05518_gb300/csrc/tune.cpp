@@ -45,9 +45,17 @@ std::vector<Cand> candidates(int nvec, int storage)
         // whole rows with the W rows staged by TMA: all vectors or half of them per CTA
         c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 6, 0}});
         c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 7, 0}});
-        if (G2 % 2 == 0 && (G2 / 2) % vb == 0 && G2 / 2 >= 2 * vb) c.push_back({TLS_KERNEL_MRHS, vb, 0, {G2 / 2, 6, 0}});
+        for (int nrow : {2, 4}) c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 6, nrow}});  // rows per CTA
+        for (int ng : {G2 / 2, 24, 12})  // fewer vectors per CTA: smaller CTAs, W staged once per group
+            if (ng < G2 && ng >= 2 * vb && ng % vb == 0 && G2 % ng == 0 && (ng != 24 || G2 / 2 != 24) &&
+                (ng != 12 || G2 / 2 != 12))
+                c.push_back({TLS_KERNEL_MRHS, vb, 0, {ng, 6, 0}});
         // packed FP32 pairs with the W broadcasts staged by the threads (any row length)
         c.push_back({TLS_KERNEL_MRHS, vb, 128, {0, 2, 0}});
+    }
+    if (storage == TLS_F32 && G2 % 8 == 0) {  // eight FP32 vectors per thread, one colour at a time
+        c.push_back({TLS_KERNEL_MRHS, 8, 0, {0, 6, 0}});
+        c.push_back({TLS_KERNEL_MRHS, 8, 0, {0, 7, 0}});
     }
     return c;
 }

@@ -49,3 +49,35 @@ def test_headline_workload_full_size_sampled(storage):
         assert rel_l2(got, want) <= tol, (v, rel_l2(got, want))
         mask = sublattice_mask(dims, corner)
         assert np.all(got[0][~mask] == 0)
+
+
+@pytest.mark.parametrize("storage", ["F32", "F16"])
+def test_full_size_gaussian_on_later_slices(storage):
+    """The same 64^3 x 96 launch configuration (24 vectors on every slice, the autotuned
+    kernel, N = 80) with dense Gaussian vectors on every slice, so that the kernel's
+    indexing for t > 0 meets non-zero data: three vectors are checked against the FP64
+    oracle on slices 37 and 95 (the last one), each slice smeared by the oracle alone."""
+    from paper_2301_05518_gb300 import tls as T
+    w = workloads.HEADLINE
+    dims = w["dims"]
+    N, sigma = w["N"], w["sigma"]
+    st = getattr(T, "TLS_" + storage)
+    U = synth.gauge_near_unit(dims, w["eps"], w["gauge_seed"], nd=4, device="cuda")
+    vecs = synth.gaussian_vectors(dims, 24, 2003, dtype=torch.complex64, device="cuda")
+    slices = [37, 95]
+    Us = U[slices].cpu().numpy()
+    src = vecs[[0, 11, 22]][:, slices].cpu().numpy().astype(np.complex128)
+    with T.Context(0) as ctx:
+        gid = ctx.load_gauge(U, 4, dims)
+        del U
+        ctx.build_twolink(gid, T.TLS_F32, T.TLS_R18, keep_U=0)
+        ctx.autotune(gid, 24, st, T.TLS_ALL_T, steps=2)
+        ctx.smear(gid, vecs, T.TLS_F32, 24, N, sigma, storage=st)
+        ctx.free_gauge(gid)
+    want = oracle.smear(oracle.twolink(Us), src, N, sigma)
+    got = vecs[[0, 11, 22]][:, slices].cpu().numpy().astype(np.complex128)
+    tol = 2e-6 * N if storage == "F32" else 5e-3
+    for k in range(3):
+        for s in range(len(slices)):
+            e = rel_l2(got[k, s], want[k, s])
+            assert e <= tol, (k, slices[s], e)

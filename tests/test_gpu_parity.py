@@ -512,11 +512,12 @@ def test_row_tma_kernel_bitwise_equal_single(ctx, T, dims, nvec, storage, wprec,
     for t0 in (-1, dims[3] - 1):
         b = vecs.clone().cuda()
         ctx.smear(gid, b, T.TLS_F32, nvec, 7, 1.4, timeslice=t0, storage=st, kernel=T.TLS_KERNEL_SINGLE)
-        for variant in (6, 7):  # one CTA per row, registers capped for 3 or 2 CTAs of 256 threads
-            ctx.tune_set(gid, nvec, st, t0, T.TLS_KERNEL_MRHS, vb, 0, (nvg, variant, 0))
+        # one row per CTA (registers for 4 or 3 CTAs per SM, next-hop prefetch), 2 and 3 rows per CTA
+        for variant, rows in ((6, 0), (7, 0), (6, 2), (6, 3)):
+            ctx.tune_set(gid, nvec, st, t0, T.TLS_KERNEL_MRHS, vb, 0, (nvg, variant, rows))
             a = vecs.clone().cuda()
             ctx.smear(gid, a, T.TLS_F32, nvec, 7, 1.4, timeslice=t0, storage=st, kernel=T.TLS_KERNEL_AUTO)
-            assert torch.equal(a, b), variant
+            assert torch.equal(a, b), (variant, rows)
     ctx.free_gauge(gid)
     if storage == "F32" and recon == 18:  # the last slice (smeared alone) against the oracle
         want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), 7, 1.4)
