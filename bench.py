@@ -76,6 +76,7 @@ def dist_setup(backend):
 # tile); a configuration without a capture of its current code reports null.
 PROFILED_TRAFFIC_PER_SITE = {
     ("mrhs", 4, (0, 2, 0)): 1337.3,  # k_step_ilx, profiles/k_step_ilx_64x64x64x4_24vec_f32.md
+    ("mrhs", 4, (0, 6, 0)): 1337.7,  # k_step_ilt, profiles/k_step_ilt_64x64x64x4_24vec_f32.md
 }
 
 
@@ -323,11 +324,11 @@ def reference_arm(args):
     return 0
 
 
-def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0, n_check=3):
+def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0, n_check=3, inflight=24):
     """Continuous-batching serving on resident gauge fields (Poisson arrivals).
 
-    Phase 1 keeps 8 jobs in flight to measure the saturation rate X_sat
-    (vectors/s); phase 2 submits n_open jobs at Poisson times with rate
+    Phase 1 keeps `inflight` jobs in flight to measure the saturation rate
+    X_sat (vectors/s); phase 2 submits n_open jobs at Poisson times with rate
     0.7 * X_sat / E[nvec] and reports submit->result latency.  Each job's
     vectors are drawn on a client stream of their own, and the client waits
     for that stream only before it submits: the scheduler's batches run on
@@ -382,7 +383,7 @@ def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0, n
     specs1 = [spec() for _ in range(n_closed)]
     it = iter(specs1)
     while True:
-        while len(pending) < 8:
+        while len(pending) < inflight:
             sp = next(it, None)
             if sp is None:
                 break
@@ -400,6 +401,7 @@ def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0, n
             pending = []
             break
     x_sat = done_vecs / (time.perf_counter() - t0)
+    closed_jobs = len(specs1)
     # phase 2: open-loop Poisson
     specs2 = [spec() for _ in range(n_open)]
     mean_nvec = np.mean([s_[1] for s_ in specs2])
@@ -444,7 +446,8 @@ def serving_run(T, device, n_closed, n_open, time_cap_s=60.0, fp64_cap_s=15.0, n
     vec_total = sum(n for _, n in results)
     out = {"workload": "Poisson jobs on resident 16^3x32, 32^3x64, 48^3x96 Haar fields; 1-24 vectors, "
                        "N 10-80, sigma/N 0.05-0.3, FP32/FP16 50:50, cap 120 GB",
-           "x_sat_vectors_per_s": x_sat, "rate_jobs_per_s": lam, "jobs": len(results),
+           "x_sat_vectors_per_s": x_sat, "x_sat_jobs_in_flight": inflight, "x_sat_jobs": closed_jobs,
+           "rate_jobs_per_s": lam, "jobs": len(results),
            "jobs_planned": n_open,
            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
            "max_ms": float(lat.max()), "vectors_per_s": vec_total / span_s}
@@ -805,7 +808,7 @@ def our_arm(args):
         torch.cuda.empty_cache()
         extra["large_mrhs"] = large_mrhs_run(T, ctx, local, stream, hbm_peak)
         torch.cuda.empty_cache()
-        extra["serving"] = serving_run(T, local, n_closed=24, n_open=args.serve_jobs, time_cap_s=150.0,
+        extra["serving"] = serving_run(T, local, n_closed=72, n_open=args.serve_jobs, time_cap_s=150.0,
                                        fp64_cap_s=10.0)
         result["serving_p50_ms"] = extra["serving"]["p50_ms"]
         result["serving_p99_ms"] = extra["serving"]["p99_ms"]

@@ -477,58 +477,48 @@ __device__ __forceinline__ bool ilt_wait(uint64_t *bar, unsigned parity)
     return true;
 }
 
-// nrow consecutive rows y' = blockIdx.y * nrow + r per CTA: the W rows of all
-// of them are copied at the start (one mbarrier per row), so only the first
-// row waits for its copies; the others find theirs landed.
 template <int VP, int WF, int VB, bool ACT, int MAXT, int MINB, bool PF = false>
 __global__ void __launch_bounds__(MAXT, MINB) k_step_ilt(const char *__restrict__ W, const char *__restrict__ in,
                                                         char *__restrict__ out, const float *__restrict__ alphaf,
-                                                        const int *__restrict__ active, SubGeom g, int nvec, int nrow,
-                                                        int *err)
+                                                        const int *__restrict__ active, SubGeom g, int nvec, int *err)
 {
     static_assert(VP != P_F64, "packed FP32 pairs only");
-    constexpr int WB = wfmt_bytes(WF);
     extern __shared__ __align__(128) unsigned char ilt_sm[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(ilt_sm);  // one per row (nrow <= 16)
-    char *ws0 = reinterpret_cast<char *>(ilt_sm) + 128;
-    const int setsB = 5 * g.hx * WB;
-    const int y0 = blockIdx.y * nrow;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(ilt_sm);
+    char *ws = reinterpret_cast<char *>(ilt_sm) + 128;
+    const int yq = blockIdx.y;
     const int blk = blockIdx.z / g.hz;
     const int zq = blockIdx.z - blk * g.hz;
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
     if (leader) {
-        for (int r = 0; r < nrow; ++r) mbar_init(&bar[r], 1);
+        mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (leader)
-        for (int r = 0; r < nrow; ++r) ilt_issue_w<WF>(ws0 + r * setsB, W, g, blk, zq, y0 + r, &bar[r]);
+    if (leader) ilt_issue_w<WF>(ws, W, g, blk, zq, yq, bar);
 
     const int k = threadIdx.y;                           // x' of this thread's site
     const int t = blockIdx.x * blockDim.x + threadIdx.x;  // vector unit over the whole site
     const int T = nvec / VB;
+    IltSite<VP, WF, VB, ACT, PF> st;
+    st.setup(in, out, active, g, nvec, blk, zq, yq, k, t, T);
+    // The first warp waits for the copies; the others wait at the CTA barrier
+    // without spending issue slots.  The CTA must not retire while its copies
+    // are in flight: on a timeout the leader waits once more (bounded).
     __shared__ int w_ok;
-    for (int r = 0; r < nrow; ++r) {
-        IltSite<VP, WF, VB, ACT, PF> st;
-        st.setup(in, out, active, g, nvec, blk, zq, y0 + r, k, t, T);
-        // The first warp waits for the row's copies; the others wait at the
-        // CTA barrier without spending issue slots.  The CTA must not retire
-        // while its copies are in flight: on a timeout the leader waits once
-        // more (bounded) for every row still pending.
-        if (threadIdx.x + threadIdx.y * blockDim.x < 32) {
-            const bool okw = ilt_wait(&bar[r], 0u);
-            if (leader) {
-                w_ok = okw;
-                if (!okw) {
-                    atomicOr(err, DERR_TIMEOUT);
-                    for (int q = r; q < nrow; ++q) ilt_wait(&bar[q], 0u);
-                }
+    if (threadIdx.x + threadIdx.y * blockDim.x < 32) {
+        const bool okw = ilt_wait(bar, 0u);
+        if (leader) {
+            w_ok = okw;
+            if (!okw) {
+                atomicOr(err, DERR_TIMEOUT);
+                ilt_wait(bar, 0u);
             }
         }
-        __syncthreads();
-        if (!w_ok) return;
-        if (st.any) st.compute(ws0 + r * setsB, g.hx, k, t, T, alphaf);
     }
+    __syncthreads();
+    if (!w_ok) return;
+    if (st.any) st.compute(ws, g.hx, k, t, T, alphaf);
 }
 
 // Vectors per CTA: tile[0] if it is a multiple of VB dividing nvec, else the
@@ -553,38 +543,34 @@ template <int VP, int WF, int VB> cudaError_t ilt_launch(const StepArgs &a)
         if (!a.err || !a.alphaf || !ilt_ok(WF, a.g)) return cudaErrorNotSupported;
         const int nvg = ilt_group(a.nvec, VB, a.g.hx, a.tile[0]);
         if (nvg == 0) return cudaErrorNotSupported;
-        // tile[2] = rows per CTA (1 by default; it must divide hy and fit the shared memory)
-        int nrow = a.tile[2] > 0 ? std::min(a.tile[2], 16) : 1;
-        while (nrow > 1 && (a.g.hy % nrow != 0 || 128 + nrow * (ilt_smem(a.g.hx, wfmt_bytes(WF)) - 128) > (48 << 10)))
-            --nrow;
         dim3 block(nvg / VB, a.g.hx);
-        dim3 grid(a.nvec / nvg, a.g.hy / nrow, (unsigned)a.g.hz * a.nblk);
+        dim3 grid(a.nvec / nvg, a.g.hy, (unsigned)a.g.hz * a.nblk);
         if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-        const int smem = 128 + nrow * (ilt_smem(a.g.hx, wfmt_bytes(WF)) - 128);
+        const int smem = ilt_smem(a.g.hx, wfmt_bytes(WF));
         if (smem > (48 << 10)) return cudaErrorNotSupported;
         const bool act = a.active != nullptr;
         const int threads = block.x * block.y;
         if (a.tile[1] == 7 && threads <= 192) {  // registers for 3 CTAs of 192 threads per SM
             if (act)
                 k_step_ilt<VP, WF, VB, true, 192, 3, true><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, nrow, a.err);
+                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
             else
                 k_step_ilt<VP, WF, VB, false, 192, 3, true><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, nrow, a.err);
+                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
         } else if (a.tile[1] == 7) {  // registers for 2 CTAs of 256 threads per SM
             if (act)
                 k_step_ilt<VP, WF, VB, true, 256, 2, true><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, nrow, a.err);
+                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
             else
                 k_step_ilt<VP, WF, VB, false, 256, 2, true><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, nrow, a.err);
+                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
         } else {  // registers for 3 CTAs of 256 threads per SM
             if (act)
                 k_step_ilt<VP, WF, VB, true, 256, 3><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, nrow, a.err);
+                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
             else
                 k_step_ilt<VP, WF, VB, false, 256, 3><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, nrow, a.err);
+                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
         }
         return cudaGetLastError();
     }
