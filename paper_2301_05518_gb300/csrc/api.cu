@@ -720,7 +720,7 @@ tls_status smear_impl(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_prec, in
         if (threads <= 0) threads = 128;
     } else if (kern == TLS_KERNEL_MRHS || kern == TLS_KERNEL_MRHS_ROWS || kern == TLS_KERNEL_MRHS_ZM) {
         // eight vectors per thread: FP32 storage, packed kernel (tile[1] = 2) only
-        const bool vb8 = vb == 8 && storage == TLS_F32 && (tile[1] == 2 || tile[1] == 6 || tile[1] == 7) &&
+        const bool vb8 = vb == 8 && storage == TLS_F32 && (tile[1] == 2 || (tile[1] >= 6 && tile[1] <= 8)) &&
                          kern == TLS_KERNEL_MRHS;
         if (vb <= 0 || (vb > 4 && !vb8) || G0 % vb != 0 || (storage == TLS_F64 && vb > 2))
             vb = default_il_vb(storage, G0);

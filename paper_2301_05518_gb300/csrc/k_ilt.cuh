@@ -129,6 +129,41 @@ template <int VP, int WF, int VB, bool ACT, bool PF = false> struct IltSite {
         }
     }
     int tt, TT;
+    // RB: the records of the site's own row in shared memory (the global
+    // layout of the row, colour planes rcs elements apart), for the x
+    // neighbours and the centre
+    const char *rbuf = nullptr;
+    int rcs = 0;
+    __device__ __forceinline__ void load_rec_row(int kk, float2 (&pre)[NP][3], float2 (&pim)[NP][3])
+    {
+        const char *s = rbuf + (unsigned)kk * rstride;
+        if constexpr (PAIRS && VP != P_F32) {
+#pragma unroll
+            for (int j = 0; j < NP; ++j) VRec<VP>::template load_pairs<false>(s, tt + j * TT, pre[j], pim[j]);
+        } else if constexpr (PAIRS) {
+            if constexpr (VB % 4 == 0) {
+#pragma unroll
+                for (int j = 0; j < VB / 4; ++j)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float4 *p = reinterpret_cast<const float4 *>(s) + (c * rcs + 4 * (VB / 4 * tt + j)) / 2;
+                        const float4 a = p[0], b = p[1];
+                        pre[2 * j][c] = make_float2(a.x, a.y);
+                        pim[2 * j][c] = make_float2(a.z, a.w);
+                        pre[2 * j + 1][c] = make_float2(b.x, b.y);
+                        pim[2 * j + 1][c] = make_float2(b.z, b.w);
+                    }
+            } else {
+                const float4 *p = reinterpret_cast<const float4 *>(s) + tt;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float4 q = p[c * (rcs >> 1)];
+                    pre[0][c] = make_float2(q.x, q.y);
+                    pim[0][c] = make_float2(q.z, q.w);
+                }
+            }
+        }
+    }
 
     __device__ __forceinline__ void setup(const char *__restrict__ in, char *__restrict__ out,
                                           const int *__restrict__ active, const SubGeom &g, int nvec, int blk, int zq,
@@ -158,7 +193,7 @@ template <int VP, int WF, int VB, bool ACT, bool PF = false> struct IltSite {
         }
         tt = t;
         TT = T;
-        if (any) {
+        if (any && !rbuf) {  // RB: the first hops come from the staged row
             if constexpr (COLS)
                 load_col(rin + (unsigned)nb[0] * rstride, 0, pre0, pim0);
             else
@@ -307,17 +342,20 @@ template <int VP, int WF, int VB, bool ACT, bool PF = false> struct IltSite {
         const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
+            const bool from_row = rbuf && q < 2;  // RB: x neighbours from the staged row
             if constexpr (PF) {
                 const char *nx = rin + (unsigned)(q < 5 ? nb[q + 1] : i) * rstride;
                 if (q & 1)
                     load_rec_to(nx, pre, pim);
                 else
                     load_rec_to(nx, qre, qim);
+            } else if (from_row) {
+                load_rec_row(q == 0 ? (k == hx - 1 ? 0 : k + 1) : km, qre, qim);
             } else if (q > 0) {
                 load_rec(rin + (unsigned)nb[q] * rstride);
             }
-            float2 (&cre)[NP][3] = (PF && (q & 1)) ? qre : pre;
-            float2 (&cim)[NP][3] = (PF && (q & 1)) ? qim : pim;
+            float2 (&cre)[NP][3] = ((PF && (q & 1)) || from_row) ? qre : pre;
+            float2 (&cim)[NP][3] = ((PF && (q & 1)) || from_row) ? qim : pim;
             const bool dag = q & 1;
             const char *wset = ws + (q == 0 ? 0 : q - 1) * setB;
             const int wk = q == 1 ? km : k;
@@ -352,7 +390,12 @@ template <int VP, int WF, int VB, bool ACT, bool PF = false> struct IltSite {
                 }
             }
         }
-        if constexpr (!PF) load_rec(rin + (unsigned)i * rstride);  // the centre (PF: loaded during hop 5)
+        if constexpr (!PF) {  // the centre (PF: loaded during hop 5)
+            if (rbuf)
+                load_rec_row(k, pre, pim);
+            else
+                load_rec(rin + (unsigned)i * rstride);
+        }
         const float2 m6 = make_float2(-6.f, -6.f);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
@@ -477,11 +520,15 @@ __device__ __forceinline__ bool ilt_wait(uint64_t *bar, unsigned parity)
     return true;
 }
 
-template <int VP, int WF, int VB, bool ACT, int MAXT, int MINB, bool PF = false>
+// RB (one vector group per row, vector pairs): the row's own records are
+// copied into shared memory with the W rows, and the x neighbours and the
+// centre are read from there.
+template <int VP, int WF, int VB, bool ACT, int MAXT, int MINB, bool PF = false, bool RB = false>
 __global__ void __launch_bounds__(MAXT, MINB) k_step_ilt(const char *__restrict__ W, const char *__restrict__ in,
                                                         char *__restrict__ out, const float *__restrict__ alphaf,
                                                         const int *__restrict__ active, SubGeom g, int nvec, int *err)
 {
+    static_assert(!RB || (VB % 2 == 0 && !PF), "row staging: vector pairs, no next-hop prefetch");
     static_assert(VP != P_F64, "packed FP32 pairs only");
     extern __shared__ __align__(128) unsigned char ilt_sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(ilt_sm);
@@ -495,12 +542,33 @@ __global__ void __launch_bounds__(MAXT, MINB) k_step_ilt(const char *__restrict_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (leader) ilt_issue_w<WF>(ws, W, g, blk, zq, yq, bar);
+    constexpr int VBY = vfmt_bytes(VP);
+    char *rbuf = ws + 5 * g.hx * wfmt_bytes(WF);
+    if (leader) {
+        if constexpr (RB) {  // the row's records: its bytes join the phase before the W arrival
+            const unsigned rowB = (unsigned)(g.hx * nvec * VBY);
+            mbar_expect_tx_only(bar, rowB);
+            const char *rb = in + (int64_t)blk * g.Ps * nvec * VBY;
+            const int64_t row = (int64_t)zq * g.hy * g.hx + (int64_t)yq * g.hx;
+            if constexpr (VP == P_F32) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    bulk_load(rbuf + c * (rowB / 3), rb + ((int64_t)c * g.Ps + row) * nvec * 8, rowB / 3, bar);
+            } else {
+                bulk_load(rbuf, rb + row * nvec * VBY, rowB, bar);
+            }
+        }
+        ilt_issue_w<WF>(ws, W, g, blk, zq, yq, bar);
+    }
 
     const int k = threadIdx.y;                           // x' of this thread's site
     const int t = blockIdx.x * blockDim.x + threadIdx.x;  // vector unit over the whole site
     const int T = nvec / VB;
     IltSite<VP, WF, VB, ACT, PF> st;
+    if constexpr (RB) {
+        st.rbuf = rbuf;
+        st.rcs = g.hx * nvec;
+    }
     st.setup(in, out, active, g, nvec, blk, zq, yq, k, t, T);
     // The first warp waits for the copies; the others wait at the CTA barrier
     // without spending issue slots.  The CTA must not retire while its copies
@@ -550,6 +618,19 @@ template <int VP, int WF, int VB> cudaError_t ilt_launch(const StepArgs &a)
         if (smem > (48 << 10)) return cudaErrorNotSupported;
         const bool act = a.active != nullptr;
         const int threads = block.x * block.y;
+        if constexpr (VB % 2 == 0) {
+            // tile[1] = 8: the row's own records staged with the W rows (one vector group per row)
+            const int smem_rb = smem + a.g.hx * a.nvec * vfmt_bytes(VP);
+            if (a.tile[1] == 8 && nvg == a.nvec && smem_rb <= (48 << 10)) {
+                if (act)
+                    k_step_ilt<VP, WF, VB, true, 256, 3, false, true><<<grid, block, smem_rb, a.stream>>>(
+                        a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
+                else
+                    k_step_ilt<VP, WF, VB, false, 256, 3, false, true><<<grid, block, smem_rb, a.stream>>>(
+                        a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
+                return cudaGetLastError();
+            }
+        }
         if (a.tile[1] == 7 && threads <= 192) {  // registers for 3 CTAs of 192 threads per SM
             if (act)
                 k_step_ilt<VP, WF, VB, true, 192, 3, true><<<grid, block, smem, a.stream>>>(

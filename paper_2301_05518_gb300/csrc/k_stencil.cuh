@@ -994,7 +994,7 @@ template <int VP, int WF, int VB, bool ONLYX = false> cudaError_t step_il_launch
 {
     // whole-row CTAs with the W rows staged by TMA bulk copies (k_ilt.cuh); a
     // shape or format it does not cover runs the packed kernel instead
-    const bool ilt = a.tile[1] == 6 || a.tile[1] == 7;
+    const bool ilt = a.tile[1] == 6 || a.tile[1] == 7 || a.tile[1] == 8;
     if (ilt) {
         const cudaError_t e = ilt_launch<VP, WF, VB>(a);
         if (e != cudaErrorNotSupported) return e;

@@ -23,6 +23,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
                  : "memory");
 }
 
+// Raises the transaction bytes the current phase waits for, without arriving.
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");

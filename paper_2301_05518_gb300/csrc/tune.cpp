@@ -45,6 +45,7 @@ std::vector<Cand> candidates(int nvec, int storage)
         // whole rows with the W rows staged by TMA: all vectors or half of them per CTA
         c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 6, 0}});
         c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 7, 0}});
+        if (vb % 2 == 0) c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 8, 0}});  // the row's records staged too
         for (int ng : {G2 / 2, 24, 12})  // fewer vectors per CTA: smaller CTAs, W staged once per group
             if (ng < G2 && ng >= 2 * vb && ng % vb == 0 && G2 % ng == 0 && (ng != 24 || G2 / 2 != 24) &&
                 (ng != 12 || G2 / 2 != 12))

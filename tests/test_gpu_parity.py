@@ -512,8 +512,9 @@ def test_row_tma_kernel_bitwise_equal_single(ctx, T, dims, nvec, storage, wprec,
     for t0 in (-1, dims[3] - 1):
         b = vecs.clone().cuda()
         ctx.smear(gid, b, T.TLS_F32, nvec, 7, 1.4, timeslice=t0, storage=st, kernel=T.TLS_KERNEL_SINGLE)
-        # registers for 4 CTAs per SM; the next hop's records prefetched (3 CTAs per SM)
-        for variant, rows in ((6, 0), (7, 0)):
+        # registers for 4 CTAs per SM; the next hop's records prefetched (3 CTAs per SM);
+        # the row's own records staged in shared memory with the W rows
+        for variant, rows in ((6, 0), (7, 0), (8, 0)):
             ctx.tune_set(gid, nvec, st, t0, T.TLS_KERNEL_MRHS, vb, 0, (nvg, variant, rows))
             a = vecs.clone().cuda()
             ctx.smear(gid, a, T.TLS_F32, nvec, 7, 1.4, timeslice=t0, storage=st, kernel=T.TLS_KERNEL_AUTO)
@@ -523,6 +524,19 @@ def test_row_tma_kernel_bitwise_equal_single(ctx, T, dims, nvec, storage, wprec,
         want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), 7, 1.4)
         got = a.cpu().numpy().astype(np.complex128)
         assert max(per_vector_rel_l2(got[:, -1:], want[:, -1:])) <= 2e-6 * 7
+
+
+def test_peak_flops_measures_the_fma_rates(T):
+    """tls_peak_flops: positive rates, packed FP32 at least the scalar FP32 rate within the
+    timing noise, and FP32 well above FP64 on this GPU (the roof of the FP64 kernels)."""
+    f64 = T.tls_peak_flops(0, T.TLS_PEAK_F64)
+    f32 = T.tls_peak_flops(0, T.TLS_PEAK_F32)
+    f2 = T.tls_peak_flops(0, T.TLS_PEAK_F32X2)
+    assert f64 > 0 and f32 > 0 and f2 > 0
+    assert f2 >= 0.9 * f32
+    assert f32 > 4 * f64
+    with pytest.raises(T.TLSError):
+        T.tls_peak_flops(0, 7)
 
 
 # ------------------------------------------------------------------ one-link Gaussian smearing (Eq. 2-3)
