@@ -93,7 +93,7 @@ def kernel_symbol(kern_name: str, entry: dict) -> str:
     """CUDA kernel that a tune-table entry launches (the name ncu lists)."""
     if kern_name == "mrhs":
         tile = tuple(entry.get("tile", (0, 0, 0)))
-        if tile[1] in (6, 7):
+        if tile[1] in (6, 7, 8):
             return "k_step_ilt"
         if tile[1] == 5:
             return "k_step_ilx_occ"

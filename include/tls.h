@@ -288,8 +288,10 @@ typedef struct {
                             /* tile[1] = 6 runs one CTA per whole x'-row with  */
                             /* the row's five W rows copied in by TMA bulk     */
                             /* copies (tile[0] > 0: vectors per CTA), 7 the    */
-                            /* same with a looser register cap (FP32 and       */
-                            /* 16-bit storage; other shapes take tile[1] = 2); */
+                            /* same with the next hop's records requested      */
+                            /* early, 8 with the row's own records copied in   */
+                            /* as well (FP32 and 16-bit storage; other shapes  */
+                            /* take tile[1] = 2);                              */
                             /* tile[2] unused                                  */
     double ms_per_step;     /* measured time of one smearing step              */
 } tls_tune_entry;

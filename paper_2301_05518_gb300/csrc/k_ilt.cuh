@@ -537,11 +537,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_step_ilt(const char *__restrict_
     const int blk = blockIdx.z / g.hz;
     const int zq = blockIdx.z - blk * g.hz;
     const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+    // Only the leader touches the mbarrier (initialises it, issues the copies
+    // and waits), so no CTA barrier is needed before the copies start.
     if (leader) {
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
     constexpr int VBY = vfmt_bytes(VP);
     char *rbuf = ws + 5 * g.hx * wfmt_bytes(WF);
     if (leader) {
@@ -570,18 +571,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_step_ilt(const char *__restrict_
         st.rcs = g.hx * nvec;
     }
     st.setup(in, out, active, g, nvec, blk, zq, yq, k, t, T);
-    // The first warp waits for the copies; the others wait at the CTA barrier
-    // without spending issue slots.  The CTA must not retire while its copies
-    // are in flight: on a timeout the leader waits once more (bounded).
+    // The leader waits for the copies; the other threads wait at the CTA
+    // barrier without spending issue slots.  The CTA must not retire while its
+    // copies are in flight: on a timeout the leader waits once more (bounded).
     __shared__ int w_ok;
-    if (threadIdx.x + threadIdx.y * blockDim.x < 32) {
+    if (leader) {
         const bool okw = ilt_wait(bar, 0u);
-        if (leader) {
-            w_ok = okw;
-            if (!okw) {
-                atomicOr(err, DERR_TIMEOUT);
-                ilt_wait(bar, 0u);
-            }
+        w_ok = okw;
+        if (!okw) {
+            atomicOr(err, DERR_TIMEOUT);
+            ilt_wait(bar, 0u);
         }
     }
     __syncthreads();

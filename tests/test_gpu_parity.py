@@ -512,7 +512,7 @@ def test_row_tma_kernel_bitwise_equal_single(ctx, T, dims, nvec, storage, wprec,
     for t0 in (-1, dims[3] - 1):
         b = vecs.clone().cuda()
         ctx.smear(gid, b, T.TLS_F32, nvec, 7, 1.4, timeslice=t0, storage=st, kernel=T.TLS_KERNEL_SINGLE)
-        # registers for 4 CTAs per SM; the next hop's records prefetched (3 CTAs per SM);
+        # 6: the default launch bounds; 7: the next hop's records requested early;
         # the row's own records staged in shared memory with the W rows
         for variant, rows in ((6, 0), (7, 0), (8, 0)):
             ctx.tune_set(gid, nvec, st, t0, T.TLS_KERNEL_MRHS, vb, 0, (nvg, variant, rows))
