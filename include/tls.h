@@ -224,9 +224,9 @@ tls_status tls_smear_onelink(tls_ctx *ctx, tls_gauge_id id, void *vecs, int io_p
  * library holds until the process exits; a smear whose packed vectors and
  * persistent-kernel scratch do not fit is rejected with TLS_ERR_ARG (use
  * tls_smear for it).  The first call on a device looks up the array's device
- * address with that device current, so make that first call before any
- * stream capture.  Calls share the array: each clears what must start at
- * zero, and calls whose work overlaps on the GPU race on it.  The gauge must
+ * address with that device current.  Calls share the array: each clears
+ * what must start at zero, and calls whose work overlaps on the GPU race on
+ * it.  The gauge must
  * already be built (tls_build_twolink allocates W; this call does not).
  * Synchronous on `stream`: it waits for the stream and copies the device
  * error word into host memory before it returns.  Errors as tls_smear; after
@@ -292,7 +292,11 @@ typedef struct {
                             /* early, 8 with the row's own records copied in   */
                             /* as well (FP32 and 16-bit storage; other shapes  */
                             /* take tile[1] = 2);                              */
-                            /* tile[2] unused                                  */
+                            /* tile[2] (tile[1] = 6..8): each CTA requests     */
+                            /* into L2 the W rows and records of the row       */
+                            /* tile[2] planes ahead in launch order; 0 none,   */
+                            /* < 0 the distance that keeps about 12 MB of row  */
+                            /* data ahead; other kernels ignore it             */
     double ms_per_step;     /* measured time of one smearing step              */
 } tls_tune_entry;
 

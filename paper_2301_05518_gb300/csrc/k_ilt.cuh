@@ -75,6 +75,41 @@ __device__ __forceinline__ void ilt_issue_w(char *ws, const char *__restrict__ W
     }
 }
 
+// Requests into L2 the data that the CTA pfd planes (grid z) further on in
+// launch order reads first: the W rows of the three directions at its row
+// and the records of its row (all vectors).  Every row of the launch is
+// requested once, by the CTA pfd planes before it, so the DRAM reads run
+// ahead of the CTAs that use them.  Issued by the leader of the CTAs with
+// blockIdx.x == 0; a request is a hint and changes no result.
+template <int VP, int WF>
+__device__ __forceinline__ void ilt_prefetch_ahead(const char *__restrict__ W, const char *__restrict__ in,
+                                                   const SubGeom &g, int nvec, int pfd)
+{
+    const unsigned z2 = blockIdx.z + (unsigned)pfd;
+    if (z2 >= gridDim.z) return;
+    const int blk = (int)z2 / g.hz, zq = (int)z2 - blk * g.hz;
+    const int64_t row = (int64_t)zq * g.hy * g.hx + (int64_t)blockIdx.y * g.hx;
+    constexpr int WB = wfmt_bytes(WF), NQ = WB / 16, REM = WB % 16;
+    const char *wb = W + (int64_t)blk * 3 * g.Ps * WB;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const char *wd = wb + (int64_t)d * g.Ps * WB;
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) l2_prefetch(wd + ((int64_t)j * g.Ps + row) * 16, (unsigned)(g.hx * 16));
+        if constexpr (REM > 0) l2_prefetch(wd + (int64_t)NQ * g.Ps * 16 + row * REM, (unsigned)(g.hx * REM));
+    }
+    constexpr int VBY = vfmt_bytes(VP);
+    const char *rb = in + (int64_t)blk * g.Ps * nvec * VBY;
+    if constexpr (VP == P_F32) {
+        if (nvec % 2 == 0)  // 16-byte aligned colour-plane rows
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                l2_prefetch(rb + ((int64_t)c * g.Ps + row) * nvec * 8, (unsigned)(g.hx * nvec * 8));
+    } else {
+        l2_prefetch(rb + row * nvec * VBY, (unsigned)(g.hx * nvec * VBY));
+    }
+}
+
 // One thread's part of a row: site x' = k of row (blk, zq, yq), vector units
 // t of T (VB vectors each), W rows staged at ws.  pl holds the records of the
 // first hop (requested before the wait on the copies).
@@ -526,7 +561,8 @@ __device__ __forceinline__ bool ilt_wait(uint64_t *bar, unsigned parity)
 template <int VP, int WF, int VB, bool ACT, int MAXT, int MINB, bool PF = false, bool RB = false>
 __global__ void __launch_bounds__(MAXT, MINB) k_step_ilt(const char *__restrict__ W, const char *__restrict__ in,
                                                         char *__restrict__ out, const float *__restrict__ alphaf,
-                                                        const int *__restrict__ active, SubGeom g, int nvec, int *err)
+                                                        const int *__restrict__ active, SubGeom g, int nvec, int *err,
+                                                        int pfd)
 {
     static_assert(!RB || (VB % 2 == 0 && !PF), "row staging: vector pairs, no next-hop prefetch");
     static_assert(VP != P_F64, "packed FP32 pairs only");
@@ -560,6 +596,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_step_ilt(const char *__restrict_
             }
         }
         ilt_issue_w<WF>(ws, W, g, blk, zq, yq, bar);
+        if (pfd > 0 && blockIdx.x == 0) ilt_prefetch_ahead<VP, WF>(W, in, g, nvec, pfd);
     }
 
     const int k = threadIdx.y;                           // x' of this thread's site
@@ -601,7 +638,9 @@ inline int ilt_group(int nvec, int vb, int hx, int want)
 
 // tile[1] = 6: registers capped for 3 CTAs of 256 threads per SM; 7: the next
 // hop's records prefetched, registers for 3 CTAs of 192 threads (2 of 256
-// when the row needs more threads).
+// when the row needs more threads); 8: the row's own records staged with the
+// W rows.  tile[2] > 0: each CTA requests into L2 the row data of the CTA
+// tile[2] planes ahead; < 0: the distance that keeps about 12 MB ahead.
 template <int VP, int WF, int VB> cudaError_t ilt_launch(const StepArgs &a)
 {
     if constexpr (VP == P_F64 || (VB > 4 && !(VP == P_F32 && VB == 8))) {
@@ -617,40 +656,48 @@ template <int VP, int WF, int VB> cudaError_t ilt_launch(const StepArgs &a)
         if (smem > (48 << 10)) return cudaErrorNotSupported;
         const bool act = a.active != nullptr;
         const int threads = block.x * block.y;
+        // L2 prefetch distance in planes: tile[2] > 0 as given, 0 none, < 0
+        // about 12 MB of row data ahead of the CTA that requests it
+        int pfd = a.tile[2] > 0 ? a.tile[2] : 0;
+        if (a.tile[2] < 0) {
+            const int64_t plane =
+                (int64_t)a.g.hy * a.g.hx * ((int64_t)a.nvec * vfmt_bytes(VP) + 3 * wfmt_bytes(WF));
+            pfd = (int)std::max<int64_t>(1, std::min<int64_t>(1 << 16, (int64_t(12) << 20) / plane));
+        }
         if constexpr (VB % 2 == 0) {
             // tile[1] = 8: the row's own records staged with the W rows (one vector group per row)
             const int smem_rb = smem + a.g.hx * a.nvec * vfmt_bytes(VP);
             if (a.tile[1] == 8 && nvg == a.nvec && smem_rb <= (48 << 10)) {
                 if (act)
                     k_step_ilt<VP, WF, VB, true, 256, 3, false, true><<<grid, block, smem_rb, a.stream>>>(
-                        a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
+                        a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err, pfd);
                 else
                     k_step_ilt<VP, WF, VB, false, 256, 3, false, true><<<grid, block, smem_rb, a.stream>>>(
-                        a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
+                        a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err, pfd);
                 return cudaGetLastError();
             }
         }
         if (a.tile[1] == 7 && threads <= 192) {  // registers for 3 CTAs of 192 threads per SM
             if (act)
                 k_step_ilt<VP, WF, VB, true, 192, 3, true><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
+                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err, pfd);
             else
                 k_step_ilt<VP, WF, VB, false, 192, 3, true><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
+                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err, pfd);
         } else if (a.tile[1] == 7) {  // registers for 2 CTAs of 256 threads per SM
             if (act)
                 k_step_ilt<VP, WF, VB, true, 256, 2, true><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
+                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err, pfd);
             else
                 k_step_ilt<VP, WF, VB, false, 256, 2, true><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
+                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err, pfd);
         } else {  // registers for 3 CTAs of 256 threads per SM
             if (act)
                 k_step_ilt<VP, WF, VB, true, 256, 3><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err);
+                    a.W, a.in, a.out, a.alphaf, a.active, a.g, a.nvec, a.err, pfd);
             else
                 k_step_ilt<VP, WF, VB, false, 256, 3><<<grid, block, smem, a.stream>>>(
-                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err);
+                    a.W, a.in, a.out, a.alphaf, nullptr, a.g, a.nvec, a.err, pfd);
         }
         return cudaGetLastError();
     }

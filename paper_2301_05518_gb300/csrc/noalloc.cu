@@ -14,9 +14,8 @@
 //
 // The array exists once per device that loads the library and lives until
 // the process exits.  Its device address is looked up once per device, on
-// the first call made with that device current (cudaGetSymbolAddress), so
-// that first call should happen before any stream capture starts.  Every
-// call reuses the same array, which keeps whatever the previous call left:
+// the first call made with that device current (cudaGetSymbolAddress).
+// Every call reuses the same array, which keeps whatever the previous call left:
 // the words that must start at zero (barrier, error) are cleared by each
 // call, and two calls whose work overlaps on the GPU (different streams or
 // host threads without ordering) race on the array.  When the call returns

@@ -74,6 +74,13 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
         : "memory");
 }
 
+// Asks the memory system to bring a contiguous global segment (16-byte
+// aligned, a multiple of 16 bytes) into L2; no completion is tracked.
+__device__ __forceinline__ void l2_prefetch(const void *src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 }  // namespace tls

@@ -44,6 +44,7 @@ std::vector<Cand> candidates(int nvec, int storage)
         if (vb == 1 && G2 >= 8) continue;
         // whole rows with the W rows staged by TMA: all vectors or half of them per CTA
         c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 6, 0}});
+        c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 6, -1}});  // rows ahead requested into L2
         c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 7, 0}});
         if (vb % 2 == 0) c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 8, 0}});  // the row's records staged too
         for (int ng : {G2 / 2, 24, 12})  // fewer vectors per CTA: smaller CTAs, W staged once per group
@@ -56,6 +57,7 @@ std::vector<Cand> candidates(int nvec, int storage)
     if (storage == TLS_F32 && G2 % 8 == 0) {  // eight FP32 vectors per thread, one colour at a time
         c.push_back({TLS_KERNEL_MRHS, 8, 0, {0, 6, 0}});
         c.push_back({TLS_KERNEL_MRHS, 8, 0, {0, 7, 0}});
+        c.push_back({TLS_KERNEL_MRHS, 8, 0, {0, 7, -1}});
     }
     return c;
 }

@@ -513,12 +513,13 @@ def test_row_tma_kernel_bitwise_equal_single(ctx, T, dims, nvec, storage, wprec,
         b = vecs.clone().cuda()
         ctx.smear(gid, b, T.TLS_F32, nvec, 7, 1.4, timeslice=t0, storage=st, kernel=T.TLS_KERNEL_SINGLE)
         # 6: the default launch bounds; 7: the next hop's records requested early;
-        # the row's own records staged in shared memory with the W rows
-        for variant, rows in ((6, 0), (7, 0), (8, 0)):
-            ctx.tune_set(gid, nvec, st, t0, T.TLS_KERNEL_MRHS, vb, 0, (nvg, variant, rows))
+        # 8: the row's own records staged in shared memory with the W rows;
+        # pfd > 0: the rows pfd planes ahead requested into L2 (-1: about 12 MB ahead)
+        for variant, pfd in ((6, 0), (7, 0), (8, 0), (6, 3), (8, 5), (6, -1), (7, -1)):
+            ctx.tune_set(gid, nvec, st, t0, T.TLS_KERNEL_MRHS, vb, 0, (nvg, variant, pfd))
             a = vecs.clone().cuda()
             ctx.smear(gid, a, T.TLS_F32, nvec, 7, 1.4, timeslice=t0, storage=st, kernel=T.TLS_KERNEL_AUTO)
-            assert torch.equal(a, b), (variant, rows)
+            assert torch.equal(a, b), (variant, pfd)
     ctx.free_gauge(gid)
     if storage == "F32" and recon == 18:  # the last slice (smeared alone) against the oracle
         want = oracle.smear(oracle.twolink(U.numpy()), vecs.numpy().astype(np.complex128), 7, 1.4)
