@@ -76,7 +76,8 @@ def dist_setup(backend):
 # tile); a configuration without a capture of its current code reports null.
 PROFILED_TRAFFIC_PER_SITE = {
     ("mrhs", 4, (0, 2, 0)): 1337.3,  # k_step_ilx, profiles/k_step_ilx_64x64x64x4_24vec_f32.md
-    ("mrhs", 4, (0, 6, 0)): 1337.7,  # k_step_ilt, profiles/k_step_ilt_64x64x64x4_24vec_f32.md
+    ("mrhs", 4, (0, 6, 0)): 1337.3,  # k_step_ilt, profiles/k_step_ilt_64x64x64x4_24vec_f32.md
+    ("mrhs", 4, (0, 6, -1)): 1337.7,  # k_step_ilt with the L2 prefetch, same profile
 }
 
 
