@@ -47,10 +47,15 @@ std::vector<Cand> candidates(int nvec, int storage)
         c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 6, -1}});  // rows ahead requested into L2
         c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 7, 0}});
         if (vb % 2 == 0) c.push_back({TLS_KERNEL_MRHS, vb, 0, {0, 8, 0}});  // the row's records staged too
-        for (int ng : {G2 / 2, 24, 12})  // fewer vectors per CTA: smaller CTAs, W staged once per group
-            if (ng < G2 && ng >= 2 * vb && ng % vb == 0 && G2 % ng == 0 && (ng != 24 || G2 / 2 != 24) &&
-                (ng != 12 || G2 / 2 != 12))
-                c.push_back({TLS_KERNEL_MRHS, vb, 0, {ng, 6, 0}});
+        // fewer vectors per CTA: smaller CTAs, W staged once per group (each
+        // distinct count once)
+        int tried[3], ntried = 0;
+        for (int ng : {G2 / 2, 24, 12}) {
+            if (ng >= G2 || ng < 2 * vb || ng % vb != 0 || G2 % ng != 0) continue;
+            if (std::find(tried, tried + ntried, ng) != tried + ntried) continue;
+            tried[ntried++] = ng;
+            c.push_back({TLS_KERNEL_MRHS, vb, 0, {ng, 6, 0}});
+        }
         // packed FP32 pairs with the W broadcasts staged by the threads (any row length)
         c.push_back({TLS_KERNEL_MRHS, vb, 128, {0, 2, 0}});
     }
