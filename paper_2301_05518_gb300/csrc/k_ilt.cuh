@@ -1,8 +1,8 @@
 // k_ilt.cuh -- multi-RHS smearing step with the W rows staged by TMA bulk copies.
 //
 // The step of Sec. 2 (Eq. tlSmear with Eq. tlLapl1) on the interleaved
-// (vector-innermost) layout, with the per-vector FMA sequence of site_step:
-// results are bitwise equal to every other kernel of the library.
+// (vector-innermost, vector-pair) layout, with the per-vector FMA sequence of
+// site_step: results are bitwise equal to every other kernel of the library.
 //
 // Work decomposition: a CTA owns one whole x'-row of one (slice, sublattice)
 // block and one group of the vectors; thread (threadIdx.x, threadIdx.y) takes
@@ -13,17 +13,28 @@
 //   set 2  W_y of row y' - 1       (y backward)
 //   set 3  W_z of row y'           (z forward)
 //   set 4  W_z of row y' in z' - 1 (z backward)
-// One elected thread copies them into shared memory in their stored format
-// with cp.async.bulk (one copy per 16-byte plane segment, completion counted
-// in transaction bytes on one mbarrier), so the staging takes no load/store
-// instructions of the other threads.  Each thread then reads the plain
-// (re, im) elements, one 16-byte word per two elements, and builds the
-// broadcast pairs of the packed FP32 FMAs (fma.rn.f32x2) in registers:
-//   forward  element W(r, c):     acc_r += {re, re} * {p.re, p.im} + {-im, im} * {p.im, p.re}
-//   backward element conj W(c, r): acc_r += {re, re} * {p.re, p.im} + {im, -im} * {p.im, p.re}
-// which is, lane by lane, the FMA sequence of cmac / cmacc.  The records of
-// the first hop are requested before the wait on the copies, so their latency
-// overlaps the staging.
+// The leader thread initialises one mbarrier, copies the five rows into
+// shared memory in their stored format with cp.async.bulk (one copy per
+// 16-byte plane segment, completion counted in transaction bytes) and waits;
+// the other threads request the records of their first hop and wait at the
+// CTA barrier, so the staging takes none of their load/store instructions.
+//
+// Arithmetic: a record load yields the real parts (re_a, re_b) and the
+// imaginary parts (im_a, im_b) of a vector pair.  With W element (wr, wi)
+// broadcast as {wr, wr} and {wi, wi}, one complex multiply-add is four
+// packed FMAs (fma.rn.f32x2):
+//   forward  W(r, c):      R += {wr}*re + {wi}*(-im);  I += {wr}*im + {wi}*re
+//   backward conj W(c, r): R += {wr}*re + {wi}*im;     I += {wr}*im + {wi}*(-re)
+// with the negated pair formed once per record and colour; lane by lane this
+// is the FMA sequence of cmac / cmacc.
+//
+// Variants (tile[1] of the tune entry): 6 the plain form; 7 the records of
+// the next hop requested before the current hop is applied; 8 the row's own
+// records copied in with the W rows (the centre and the x neighbours then
+// come from shared memory).  tile[2] > 0 (or < 0 for an automatic distance):
+// the leader also asks L2 for the W rows and records of the row that many
+// planes ahead in launch order, so their first DRAM touch happens before the
+// CTA that needs them waits for it.
 //
 // The wait is bounded: if it runs out the CTA sets DERR_TIMEOUT, waits once
 // more (bounded) for its own copies in flight and returns without writing.

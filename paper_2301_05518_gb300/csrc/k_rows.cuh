@@ -69,14 +69,14 @@ __global__ void __launch_bounds__(RowsBound<VB>::threads) k_step_rows(const char
     constexpr int WB = wfmt_bytes(WF);
     constexpr int VBY = vfmt_bytes(VP);
     constexpr int NQ = WPlanes<WF>::NQ, REM = WPlanes<WF>::REM;
-    extern __shared__ __align__(128) unsigned char sm[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm);
+    extern __shared__ __align__(128) unsigned char rows_sm[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(rows_sm);
     auto up = [](int n) { return (n + 127) / 128 * 128; };
     const int rowS = up(pl.rowB), wS = up(pl.wrowB);
-    char *Y = reinterpret_cast<char *>(sm) + pl.offY;
-    char *Z = reinterpret_cast<char *>(sm) + pl.offZ;
-    char *Wc = reinterpret_cast<char *>(sm) + pl.offW;
-    char *Wz = reinterpret_cast<char *>(sm) + pl.offWz;
+    char *Y = reinterpret_cast<char *>(rows_sm) + pl.offY;
+    char *Z = reinterpret_cast<char *>(rows_sm) + pl.offZ;
+    char *Wc = reinterpret_cast<char *>(rows_sm) + pl.offW;
+    char *Wz = reinterpret_cast<char *>(rows_sm) + pl.offWz;
 
     // A bounded wait already ran out somewhere: do nothing (no copy issued yet).
     {
