@@ -512,6 +512,18 @@ def test_inputs_links_are_su3(kind):
     assert np.abs(np.linalg.det(U) - 1).max() < 1e-13
 
 
+def test_inputs_haar_links_have_the_haar_trace_moments():
+    """Haar measure on SU(3): E[tr U] = 0, E[|tr U|^2] = 1 (the fundamental
+    representation is irreducible) and E[(tr U)^3] = 1 (3 x 3 x 3 holds the
+    trivial representation once, the determinant; on U(3) this would be 0).
+    65,536 links; the standard errors are about 0.004, 0.004 and 0.01."""
+    U = _gauge((16, 16, 16, 4), 84, "haar", nd=4).reshape(-1, 3, 3)
+    tr = np.trace(U, axis1=-2, axis2=-1)
+    assert abs(tr.mean()) < 0.02
+    assert abs((np.abs(tr) ** 2).mean() - 1) < 0.02
+    assert abs((tr ** 3).mean() - 1) < 0.06
+
+
 def test_inputs_near_unit_links_scale_with_eps():
     """exp(i eps H) with unit-variance Gell-Mann coefficients: |U - 1| grows like eps."""
     d1 = np.abs(_gauge((4, 4, 4, 1), 82, "near", eps=0.05) - np.eye(3)).mean()
